@@ -1,0 +1,486 @@
+#!/usr/bin/env python
+"""Benchmark: branch-gradient evaluations per second on one GB300.
+
+One step = one evaluation of log P(Y) and all 2N-2 branch-length gradient
+entries from new branch lengths (the quantity an HMC leapfrog step needs):
+matrices (Eq. 1) -> post-order pass (Eqs. 2-3) -> pre-order pass with the
+gradient (Eqs. 4, 8) -> FP64 reductions (Eq. 7).  The default workload is
+the 1,024-taxon HKY85+Gamma4 alignment with 10,000 patterns in FP32.
+
+Printed as one JSON line:
+  value      evals/s, inputs resident in HBM, one CUDA graph per step
+  e2e        evals/s through the C ABI with host buffers: each step copies
+             the branch lengths from pinned host memory and reads log P(Y)
+             and the gradient back
+  roofline   the dominant kernel (the phase with the largest device time)
+             against the measured HBM copy bandwidth
+  fp64_path  the plain FP64 path on the same workload and GPU
+  cpu_baseline the FP64 oracle on the host (bounded pattern sample)
+
+--impl reference times the oracle as the reference arm.
+Under torchrun each rank runs an independent replica (weak scaling, no
+collective on the data path; a MAX all-reduce of the elapsed time only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("branch-gradient evals/s & HBM GB/s vs plain FP64 GPU; "
+          "served p50/p99 latency")
+UNIT = "evals/s"
+
+
+def _workloads():
+    import synth
+    return {
+        "hky-1024": (synth.workload_hky_1024, "fp32"),
+        "codon-128": (synth.workload_codon_128, "fp32"),
+        "aa-256": (synth.workload_aa_256, "fp32"),
+        "jc69-8": (synth.workload_jc69_8, "fp64"),
+    }
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic bytes per evaluation (unpadded states; what the method must
+# move with partials resident in HBM).  M = R * C * S * elem bytes per node.
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(w, precision):
+    N, C, S, R = w.n_tips, w.n_patterns, w.n_states, w.n_categories
+    elem = 8 if precision == "fp64" else 4
+    M = R * C * S * elem
+    mats = (2 * N - 2) * R * S * S * elem
+    return {
+        # P and dP written (and V, Vinv, lambda, t read: negligible)
+        "pmat": 2 * mats,
+        # read p of internal children, write p of internal non-root nodes,
+        # tip states, exponents written and read, P read, pattern weights
+        "post": 2 * (N - 2) * M + N * C + 2 * (N - 2) * C * 4 + mats + C * 8,
+        # read q_k and p of internal children, write q of internal children,
+        # tip states, P and dP read, pattern weights, gradient out
+        "pre": 3 * (N - 2) * M + N * C + 2 * mats + C * 8 + (2 * N - 2) * 8,
+        "reduce": (2 * N - 1) * 8,
+    }
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed regions
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.lines = []
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}",
+               "--format=csv,noheader,nounits", "-lms", "50"]
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            if uuid:
+                cmd += ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            pass
+        self.cmd = cmd
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power)}
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_sample_run(name, seed, n_patterns):
+    """Runs in a spawned process with one BLAS/OpenMP thread."""
+    import synth  # noqa: F401
+    from oracle import phylo_oracle as O
+    w = _workloads()[name][0](seed)
+    ws = w.with_patterns(0, n_patterns)
+    t0 = time.perf_counter()
+    O.evaluate(ws.parent, ws.t, ws.Q, ws.pi, ws.rates, ws.weights,
+               ws.pattern_weights, tip_states=ws.tip_states)
+    return time.perf_counter() - t0, w.n_patterns
+
+
+def _oracle_pool():
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        return mp.get_context("spawn").Pool(1)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def cpu_baseline(name, seed=0, target_s=15.0):
+    """Oracle evaluations/s of the full workload from a bounded pattern
+    sample.  The oracle's cost is a fixed part (transition matrices) plus a
+    part linear in the pattern count, so two sample sizes are timed and the
+    full-workload time is extrapolated linearly from them."""
+    with _oracle_pool() as pool:
+        n_a = 100
+        t_a, C = pool.apply(_oracle_sample_run, (name, seed, n_a))
+        n_b = int(min(C, max(4 * n_a, n_a * target_s / max(t_a, 1e-3))))
+        t_b, C = pool.apply(_oracle_sample_run, (name, seed, n_b))
+    slope = max(t_b - t_a, 1e-9) / max(n_b - n_a, 1)
+    t_full = t_b + slope * (C - n_b)
+    return {"value": 1.0 / t_full, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle (numpy, 1 thread) timed on the first "
+                      f"{n_a} and {n_b} of {C} patterns ({t_a:.2f} s, "
+                      f"{t_b:.2f} s), full-workload time {t_full:.1f} s "
+                      f"extrapolated linearly in the pattern count"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    name = args.workload
+    budget = 150.0
+    with _oracle_pool() as pool:
+        t_cal, C = pool.apply(_oracle_sample_run, (name, 0, 100))
+        per_step = budget / (args.steps + args.warmup)
+        n = int(min(C, max(10, 100 * per_step / max(t_cal, 1e-3))))
+        for _ in range(args.warmup):
+            pool.apply(_oracle_sample_run, (name, 0, n))
+        times = []
+        for _ in range(args.steps):
+            t, _ = pool.apply(_oracle_sample_run, (name, 0, n))
+            times.append(t)
+    total = sum(times)
+    value = args.steps * (n / C) / total
+    precision = _workloads()[name][1]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps * (C / n),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "precision_of_our_arm": precision},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+                         "kind": "oracle",
+                         "sample": f"each step: one FP64 oracle evaluation "
+                                   f"on the first {n} of {C} patterns, "
+                                   f"scaled by {C}/{n}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def _traffic_record(kernel_phase, workload, precision):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles",
+                        f"{kernel_phase}_{workload}_{precision}.md")
+    if not os.path.exists(path):
+        return None
+    rec = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            rec[k.strip()] = v.strip()
+    if rec.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(rec["dram_bytes_per_launch"]), int(rec["launches"])
+    except (KeyError, ValueError):
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2303_04390_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")) and f != "phylo_api.cu":
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2303_04390_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    import paper_2303_04390_gb300 as pg
+
+    make, default_prec = _workloads()[args.workload]
+    precision = args.precision or default_prec
+    w = make(rank)  # independent replica per rank
+    stream = torch.cuda.current_stream()
+    ctx = pg.from_workload(w, precision, stream=stream)
+    K, W = args.steps, args.warmup
+    nb = 2 * w.n_tips - 2
+    # branch lengths of every step: log-normal jitter around the drawn ones
+    rng = np.random.default_rng(1000 + rank)
+    t_all = w.t[None, :] * np.exp(0.05 * rng.standard_normal((K + W, nb)))
+    t_dev = torch.tensor(t_all, dtype=torch.float64, device="cuda")
+    out = torch.empty(2 * w.n_tips - 1, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(i):
+        ctx.set_branch_lengths(t_dev[i])
+        ctx.evaluate_device(out)
+
+    sampler = ClockSampler(local)
+    for i in range(W):
+        step(i)
+    ctx.check()
+    sampler.start()
+    time.sleep(0.2)
+    # -- headline: device-resident inputs, one graph per evaluation --------
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(K):
+        step(W + i)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    ctx.check()
+    if world > 1:
+        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * K / (ms / 1e3)
+    launches = ctx.launches_per_evaluation()
+
+    # -- per-phase device times (four graph launches, events between) -----
+    n_ev = min(K, 200)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]
+           for _ in range(n_ev)]
+    barrier()
+    for i in range(n_ev):
+        ctx.set_branch_lengths(t_dev[W + i])
+        ctx.evaluate_device_timed(evs[i], out)
+    barrier()
+    phase_ms = [0.0] * 4
+    for e in evs:
+        for p in range(4):
+            phase_ms[p] += e[p].elapsed_time(e[p + 1])
+    phase_ms = [x / n_ev for x in phase_ms]
+    ctx.check()
+
+    # -- end to end through the C ABI with host buffers -------------------
+    t_host = torch.tensor(t_all, dtype=torch.float64).pin_memory()
+    ll_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    g_host = torch.empty(nb, dtype=torch.float64).pin_memory()
+    n_e2e = min(K, 500)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(n_e2e):
+        ctx.set_branch_lengths(t_host[W + i])
+        ctx.evaluate_into(ll_host, g_host)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e_value = world * n_e2e / e2e_s
+    sampler.stop()
+    clocks = sampler.summary()
+
+    # -- the plain FP64 path on the same workload -------------------------
+    fp64 = None
+    if precision != "fp64" and not args.skip_fp64:
+        ctx64 = pg.from_workload(w, "fp64", stream=stream)
+        n64 = max(5, min(K // 10, 100))
+        for i in range(3):
+            ctx64.set_branch_lengths(t_dev[i])
+            ctx64.evaluate_device(out)
+        barrier()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for i in range(n64):
+            ctx64.set_branch_lengths(t_dev[W + i])
+            ctx64.evaluate_device(out)
+        a1.record(stream)
+        barrier()
+        ms64 = a0.elapsed_time(a1)
+        ctx64.check()
+        by64 = algorithmic_bytes(w, "fp64")
+        fp64 = {"value": n64 / (ms64 / 1e3), "unit": UNIT, "steps": n64,
+                "hbm_gbs_all_phases": sum(by64.values()) / (ms64 / n64 / 1e3) / 1e9}
+        ctx64.close()
+
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_kind = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    by = algorithmic_bytes(w, precision)
+    names = ["pmat", "post", "pre", "reduce"]
+    kernels = {"pmat": "pmat_kernel", "post": "post-order level kernel",
+               "pre": "pre-order level kernel (fused gradient)",
+               "reduce": "reduce_kernel"}
+    phases = {}
+    for n_, ms_ in zip(names, phase_ms):
+        phases[n_] = {"ms": ms_, "algorithmic_bytes": by[n_],
+                      "achieved_gbs": by[n_] / (ms_ / 1e3) / 1e9 if ms_ > 0 else None}
+    dom = max(names, key=lambda n_: phases[n_]["ms"])
+    n_launch_dom = {"pmat": 1, "reduce": 1}.get(dom)
+    if n_launch_dom is None:
+        n_launch_dom = ctx.level_counts()[0 if dom == "post" else 1]
+    achieved = phases[dom]["achieved_gbs"]
+    tr = _traffic_record(dom, args.workload, precision)
+    traffic = None
+    if tr is not None:
+        traffic = tr[0]
+    roofline = {
+        "bound": "hbm", "kernel": kernels[dom], "achieved": achieved,
+        "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+        "peak_kind": f"{peak_kind} (HBM copy)",
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": by[dom] / n_launch_dom,
+        "launches_per_evaluation": n_launch_dom,
+        "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
+    }
+    cpu = None
+    if world == 1 and not args.skip_cpu:
+        cpu = cpu_baseline(args.workload)
+    s_pad = 4 if w.n_states <= 4 else 20 if w.n_states <= 20 else 64
+    part_bytes = 2 * (w.n_tips - 1) * w.n_patterns * w.n_categories * \
+        s_pad * (8 if precision == "fp64" else 4)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == "fp64" else "f32",
+        "data": "synthetic",
+        "config": {
+            "workload": args.workload, "taxa": w.n_tips,
+            "patterns": w.n_patterns, "states": w.n_states,
+            "categories": w.n_categories, "precision": precision,
+            "l2": f"inputs larger than L2: {part_bytes / 1e9:.2f} GB of "
+                  f"partials streamed per evaluation",
+            "parallelism": f"replicas x{world}",
+        },
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": nb * 8,
+                "d2h_bytes_per_step": (2 * w.n_tips - 1) * 8 + 8,
+                "steps": n_e2e},
+        "gpu_launches": K * launches,
+        "launches_per_step": launches,
+        "roofline": roofline,
+        "phases": phases,
+        "hbm_gbs_all_phases": sum(by.values()) / (ms / K / 1e3) / 1e9,
+        "fp64_path": fp64,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hky-1024",
+                    choices=["hky-1024", "codon-128", "aa-256", "jc69-8"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

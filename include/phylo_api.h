@@ -1,0 +1,178 @@
+/*
+ * phylo_api.h -- C ABI of libphylograd: the phylogenetic log-likelihood and
+ * its gradient with respect to all 2N-2 branch lengths on one GPU
+ * (arXiv 2303.04390, "Many-core algorithms for high-dimensional gradients on
+ * phylogenetic trees").
+ *
+ * Problem statement (paper, Methods): an alignment of C unique site
+ * patterns with integer weights W_c over N taxa; a rooted binary tree with
+ * tips 0..N-1, internal nodes N..2N-2 and the root 2N-2; branch i is the
+ * branch above node i (length t_i); a reversible CTMC with generator Q and
+ * root distribution pi; R rate categories with rates gamma_r and weights
+ * w_r.  P^(r)(t) = exp(gamma_r t Q) (Eq. 1), entry (s,u) = Pr(child u |
+ * parent s).  The library returns
+ *     log P(Y) = sum_c W_c log sum_r w_r pi' p_root,r,c          (Eq. 3)
+ *     d log P(Y) / d t_i  for every i < 2N-2                      (Eqs. 7, 8)
+ * via post-order partials (Eq. 2), pre-order partials (Eq. 4) and the
+ * per-branch ratio of Eq. 8, with per-node power-of-two rescaling.
+ *
+ * Conventions for every call:
+ *  - Return value: PHYLO_OK (0) or a negative phylo_status.  After an error
+ *    phylo_last_error(ctx) describes it.  Nothing aborts or exits.
+ *  - Host pointers are read during the call and not kept; the caller keeps
+ *    ownership.  Device pointers are noted as such.
+ *  - The library allocates no device memory.  The caller provides one
+ *    device workspace of phylo_workspace_bytes() bytes at phylo_create and
+ *    keeps it alive until phylo_destroy.
+ *  - All device work is ordered on the stream given to phylo_create
+ *    (NULL = the legacy default stream).
+ *  - Matrices are row-major FP64.  Sizes: N tips, C patterns, S states
+ *    (2 <= S <= 64), R categories (1 <= R <= 8).
+ */
+#ifndef PHYLO_API_H
+#define PHYLO_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct phylo_ctx phylo_ctx; /* opaque; host-side state only */
+
+enum phylo_status {
+  PHYLO_OK = 0,
+  PHYLO_EINVAL = -1,   /* an argument or input failed validation          */
+  PHYLO_ENOMEM = -2,   /* workspace too small or host allocation failed    */
+  PHYLO_ECUDA = -3,    /* a CUDA runtime call failed (message has details) */
+  PHYLO_ESTATE = -4,   /* a required input has not been set yet            */
+  PHYLO_ENUMERIC = -5  /* the device flagged a zero/NaN partial or a bad t */
+};
+
+enum phylo_precision {
+  PHYLO_FP64 = 0, /* partials, matrices and arithmetic in FP64 (baseline) */
+  PHYLO_FP32 = 1  /* FP32 partials and arithmetic, FP64 reductions        */
+};
+
+enum phylo_flags {
+  PHYLO_FLAG_TIP_PARTIALS = 1 /* reserve storage so tips may carry partials */
+};
+
+/* Bytes of device workspace a context of this shape needs.  Host only.
+ * Returns PHYLO_EINVAL for out-of-range sizes or size_t overflow. */
+int phylo_workspace_bytes(int n_tips, int n_patterns, int n_states,
+                          int n_categories, int precision, int flags,
+                          size_t* bytes);
+
+/* Create a context over a caller-owned device workspace (device pointer,
+ * 256-byte aligned, at least phylo_workspace_bytes()).  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  Host only: no CUDA call is
+ * made until the first input is uploaded.  n_patterns may be 0 (then
+ * log P(Y) = 0 and the gradient is 0). */
+int phylo_create(phylo_ctx** ctx, int n_tips, int n_patterns, int n_states,
+                 int n_categories, int precision, int flags,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* Tree topology (paper, Methods).  parent: host int32 [2N-1];
+ * parent[2N-2] = -1 (the root); every other entry names an internal node
+ * in [N, 2N-2]; each internal node has exactly two children; tips
+ * 0..N-1 have none.  Builds the level schedule (nodes grouped by height
+ * for the post-order pass and by depth for the pre-order pass). */
+int phylo_set_tree(phylo_ctx* ctx, const int32_t* parent);
+
+/* Compact tip data (Methods, gradient subsection: an observed tip is
+ * stored as one integer per pattern).  states: host uint8 [N][C], values in [0, S]; S marks a gap or
+ * unknown character (an all-ones partial). */
+int phylo_set_tip_states(phylo_ctx* ctx, const uint8_t* states);
+
+/* Partial likelihood vector for one tip (ambiguity codes, sequencing
+ * error): host FP64 [C][S], finite, >= 0, not all zero for any c.
+ * Requires PHYLO_FLAG_TIP_PARTIALS.  Overrides the tip's states. */
+int phylo_set_tip_partials(phylo_ctx* ctx, int tip, const double* partials);
+
+/* Pattern weights W_c (paper, Methods: unique columns reweighted).
+ * host FP64 [C], finite and >= 0. */
+int phylo_set_pattern_weights(phylo_ctx* ctx, const double* weights);
+
+/* Eigen-decomposition Q = V diag(lambda) Vinv and root distribution pi,
+ * used for P(t) = V diag(e^{lambda gamma t}) Vinv (Eq. 1).  Host FP64:
+ * V, Vinv [S][S], lambda [S], pi [S] (>= 0, sums to 1).  V*Vinv must be
+ * the identity within 1e-8. */
+int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
+                    const double* lambda, const double* root_freqs);
+
+/* Convenience: a reversible generator Q (host FP64 [S][S], rows summing to
+ * 0, pi_i Q_ij = pi_j Q_ji) with stationary pi (> 0) is decomposed on the
+ * host in FP64 (Jacobi on the symmetrised matrix) and passed to
+ * phylo_set_eigen.  pi is also the root distribution. */
+int phylo_set_rate_matrix(phylo_ctx* ctx, const double* Q, const double* pi);
+
+/* Host-only utility behind phylo_set_rate_matrix: writes V, Vinv [S][S]
+ * and lambda [S] for a reversible Q with stationary pi (> 0). */
+int phylo_eigen_reversible(int n_states, const double* Q, const double* pi,
+                           double* V, double* Vinv, double* lambda);
+
+/* Rate categories (paper, Methods; Yang 1994): rates gamma_r >= 0 and
+ * weights w_r >= 0 summing to 1 (within 1e-10).  Host FP64 [R] each. */
+int phylo_set_categories(phylo_ctx* ctx, const double* rates,
+                         const double* weights);
+
+/* Branch lengths t_i for i < 2N-2 (FP64 [2N-2]).  on_device = 0: host
+ * pointer (validated: finite, >= 0); on_device = 1: device pointer, copied
+ * on the stream (validated on the device; a bad value makes the next
+ * evaluation return PHYLO_ENUMERIC). */
+int phylo_set_branch_lengths(phylo_ctx* ctx, const double* t, int on_device);
+
+/* One evaluation: P and dP/dt for all branches and categories, the
+ * post-order pass with log P(Y), the pre-order pass with the gradient, and
+ * the cross-pattern FP64 reductions.  Writes log P(Y) to *log_likelihood
+ * and d log P(Y)/d t_i to gradient[i] (host FP64 [2N-2], or NULL for
+ * log P(Y) only).  Synchronises the stream. */
+int phylo_evaluate(phylo_ctx* ctx, double* log_likelihood, double* gradient);
+
+/* Same evaluation, asynchronous: writes [log P(Y), grad_0 .. grad_{2N-3}]
+ * (FP64, 2N-1 values) to the device pointer `out` on the stream and
+ * returns without synchronising.  Device-side numeric flags are reported
+ * by the next phylo_check / phylo_evaluate. */
+int phylo_evaluate_device(phylo_ctx* ctx, double* out);
+
+/* Same as phylo_evaluate_device, split into its four phases with a
+ * caller-created cudaEvent_t recorded on the stream at each boundary:
+ * events[0] before the matrix build (Eq. 1), events[1] before the
+ * post-order pass (Eqs. 2-3), events[2] before the pre-order pass with the
+ * gradient (Eqs. 4, 8), events[3] before the final reduction (Eq. 7) and
+ * events[4] after it.  `events` is a host array of 5 cudaEvent_t; the
+ * caller owns them.  The phases run as four graph launches instead of one,
+ * so per-phase device times can be read with cudaEventElapsedTime. */
+int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out,
+                                void* const* events);
+
+/* Synchronise the stream and report device-side numeric flags raised since
+ * the last check (PHYLO_ENUMERIC) or PHYLO_OK. */
+int phylo_check(phylo_ctx* ctx);
+
+/* Number of kernel launches one evaluation makes (the level schedule's
+ * length plus the matrix build and the final reduction); 0 before the
+ * tree is set. */
+int phylo_launches_per_evaluation(const phylo_ctx* ctx);
+
+/* Length of the level schedule: the number of post-order launches (tree
+ * height) and of pre-order launches (distinct depths of internal nodes).
+ * Both 0 before the tree is set. */
+int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
+                       int* n_pre_levels);
+
+/* Message for the last error on ctx (or for the last failed phylo_create
+ * when ctx is NULL).  Valid until the next call on ctx. */
+const char* phylo_last_error(const phylo_ctx* ctx);
+
+/* Release the host-side state and any CUDA objects (graph, streams) of the
+ * context.  The caller frees the workspace afterwards. */
+int phylo_destroy(phylo_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHYLO_API_H */

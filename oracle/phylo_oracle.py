@@ -9,7 +9,7 @@ eigendecomposition), carries its own log-scale factors (not powers of two),
 and evaluates the gradient in the paper's Eq. 8 form p' Q' q (the CUDA path
 uses the equivalent a' (dP) p form).
 
-Notation (paper, Section 2): tips 0..N-1, internal nodes N..2N-2, the root
+Notation (paper, Methods): tips 0..N-1, internal nodes N..2N-2, the root
 is the node whose parent is -1; branch i is the branch above node i, with
 length t[i]. For each node i, category r and pattern c:
   p[i][r, c, :]  post-order partial  (Eq. 2)
@@ -256,7 +256,7 @@ def node_likelihood_terms(p_i, q_i):
 
 def evaluate(parent, t, Q, pi, rates, weights, pattern_weights,
              tip_states=None, tip_partials=None, return_details=False):
-    """log P(Y) and d log P(Y) / d t_i for all 2N-2 branches (Eqs. 3, 6, 8).
+    """log P(Y) and d log P(Y) / d t_i for all 2N-2 branches (Eqs. 3, 7, 8).
 
     Returns (logL, grad[2N-2], abs_sum[2N-2]) where
     abs_sum[i] = sum_c W_c |d log P(Y_c) / d t_i| is the conditioning scale

@@ -1,0 +1,913 @@
+// Level-batched kernels for the post-order pass (Eq. 2, with Eq. 3 at the
+// root), the pre-order pass (Eq. 4) with the fused per-branch gradient ratio
+// (Eq. 8) and its cross-pattern reduction (Eq. 7), and the transition-matrix
+// builder (Eq. 1) of arXiv 2303.04390.
+//
+// Layout.  Partials are pattern-major, [slot][c][r][SP] with SP the padded
+// state count, so one pattern tile of every category is one contiguous
+// block of memory.  Matrices are [branch][r][SP][SP] with row = parent
+// state; padded rows and columns are zero, so padded partial entries stay 0.
+//
+// Rescaling (not in the paper): after every product the vector of (node, c)
+// is divided by 2^e, e = exponent of its max over all r and s, so one power
+// of two is shared by every category and state.  Post-order exponents are
+// accumulated per (node, c) and enter log P(Y) at the root; pre-order
+// exponents cancel in the gradient ratio and are dropped.
+//
+// Gradient.  For parent k with children i, j:
+//   a_i = q_k o (P_j p_j),  num_i = a_i' (dP_i p_i),  den = a_i' (P_i p_i)
+// which equals Eq. 8's p_i' Q' q_i / p_i' q_i with q_i = P_i' a_i, because
+// dP_i = gamma_r Q P_i and P_i commutes with Q.  g_{i,c} = sum_r w_r num /
+// sum_r w_r den; sum_c W_c g_{i,c} is reduced per tile in FP64.
+#pragma once
+
+#include <cstdint>
+
+#include "phylo_internal.h"
+
+namespace phylo {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int n = 2; };
+
+// Per-r matrix stride in shared memory: SP*SP plus 16 bytes, so that the up
+// to 8 categories read by one warp fall in different banks.
+template <typename T, int SP>
+struct MatStride { static constexpr int v = SP * SP + 16 / (int)sizeof(T); };
+
+template <typename T>
+__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+template <typename T, int SP>
+__device__ __forceinline__ void load_vec(const T* __restrict__ src, T (&v)[SP],
+                                         bool active) {
+  using V = typename Vec<T>::type;
+  constexpr int n = Vec<T>::n;
+  static_assert(SP % n == 0, "padded states must fill whole vectors");
+  if (active) {
+    const V* s = reinterpret_cast<const V*>(src);
+#pragma unroll
+    for (int i = 0; i < SP / n; ++i) {
+      V x = __ldg(s + i);
+      if constexpr (n == 4) {
+        v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
+      } else {
+        v[2 * i] = x.x; v[2 * i + 1] = x.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < SP; ++s) v[s] = T(0);
+  }
+}
+
+template <typename T, int SP>
+__device__ __forceinline__ void store_vec(T* dst, const T (&v)[SP]) {
+  using V = typename Vec<T>::type;
+  constexpr int n = Vec<T>::n;
+  V* d = reinterpret_cast<V*>(dst);
+#pragma unroll
+  for (int i = 0; i < SP / n; ++i) {
+    V x;
+    if constexpr (n == 4) {
+      x.x = v[4 * i]; x.y = v[4 * i + 1]; x.z = v[4 * i + 2]; x.w = v[4 * i + 3];
+    } else {
+      x.x = v[2 * i]; x.y = v[2 * i + 1];
+    }
+    d[i] = x;
+  }
+}
+
+// out = M v  (out[s] = sum_t M[s][t] v[t]); M row-major SP x SP in smem.
+template <typename T, int SP>
+__device__ __forceinline__ void matvec(const T* __restrict__ M,
+                                       const T (&v)[SP], T (&out)[SP]) {
+#pragma unroll
+  for (int s = 0; s < SP; ++s) {
+    T acc = T(0);
+#pragma unroll
+    for (int t = 0; t < SP; ++t) acc = fma(M[s * SP + t], v[t], acc);
+    out[s] = acc;
+  }
+}
+
+// out = M' v  (out[t] = sum_s M[s][t] v[s]).
+template <typename T, int SP>
+__device__ __forceinline__ void matvec_t(const T* __restrict__ M,
+                                         const T (&v)[SP], T (&out)[SP]) {
+#pragma unroll
+  for (int t = 0; t < SP; ++t) out[t] = T(0);
+#pragma unroll
+  for (int s = 0; s < SP; ++s) {
+#pragma unroll
+    for (int t = 0; t < SP; ++t) out[t] = fma(M[s * SP + t], v[s], out[t]);
+  }
+}
+
+// Max |v| over this lane's states, then over the RP lanes of one pattern.
+template <typename T, int SP, int RP>
+__device__ __forceinline__ T pattern_max(const T (&v)[SP], bool active) {
+  T m = T(0);
+#pragma unroll
+  for (int s = 0; s < SP; ++s) m = tmax(m, fabs(v[s]));
+  if (!active) m = T(0);
+#pragma unroll
+  for (int o = 1; o < RP; o <<= 1) m = tmax(m, __shfl_xor_sync(kFull, m, o));
+  return m;
+}
+
+// Power-of-two rescale of the pattern's vector: returns the exponent e with
+// max * 2^-e in [0.5, 1).  A zero or non-finite max raises ERR_ZERO_PARTIAL.
+template <typename T, int SP>
+__device__ __forceinline__ int rescale(T (&v)[SP], T m, bool valid_pattern,
+                                       int* err) {
+  int e = 0;
+  if (valid_pattern) {
+    if (!(m > T(0)) || !isfinite(m)) {
+      atomicOr(err, ERR_ZERO_PARTIAL);
+    } else {
+      (void)frexp(m, &e);
+    }
+  }
+  const T f = ldexp(T(1), -e);
+#pragma unroll
+  for (int s = 0; s < SP; ++s) v[s] *= f;
+  return e;
+}
+
+template <int RP>
+__device__ __forceinline__ double sum_over_lanes(double x) {
+#pragma unroll
+  for (int o = 1; o < RP; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+// Block-wide sum of one or two doubles (fixed order: deterministic).
+template <int NT>
+__device__ __forceinline__ void block_sum2(double& a, double& b,
+                                           double (*sm)[2]) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(kFull, a, o);
+    b += __shfl_down_sync(kFull, b, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sm[w][0] = a; sm[w][1] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = 0.0; b = 0.0;
+#pragma unroll
+    for (int i = 0; i < NT / 32; ++i) { a += sm[i][0]; b += sm[i][1]; }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 1: P^(r)(t_b) = V diag(e^{lambda gamma_r t_b}) Vinv and
+//        dP/dt       = V diag(gamma_r lambda e^{lambda gamma_r t_b}) Vinv,
+// for every (branch, category) in one launch, computed in FP64 and stored
+// as T with zero padding.
+// ---------------------------------------------------------------------------
+template <typename T, int SP>
+__global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
+  constexpr int UPB = (256 / (SP * SP)) > 0 ? 256 / (SP * SP) : 1;
+  __shared__ double she[UPB][SP];
+  __shared__ double shd[UPB][SP];
+  const int S = a.n_states, R = a.n_cat;
+  const int n_units = a.n_branches * R;
+  const int unit0 = blockIdx.x * UPB;
+  for (int i = threadIdx.x; i < UPB * SP; i += blockDim.x) {
+    const int u = i / SP, m = i % SP, unit = unit0 + u;
+    double e = 0.0, de = 0.0;
+    if (unit < n_units && m < S) {
+      const int b = unit / R, r = unit % R;
+      double t = a.t[b];
+      if (!(t >= 0.0) || !isfinite(t)) {
+        if (m == 0 && r == 0) atomicOr(a.err, ERR_BAD_LENGTH);
+        t = 0.0;
+      }
+      const double g = a.rates[r];
+      e = exp(a.lambda[m] * g * t);
+      de = g * a.lambda[m] * e;
+    }
+    she[u][m] = e;
+    shd[u][m] = de;
+  }
+  __syncthreads();
+  T* P = static_cast<T*>(a.P);
+  T* dP = static_cast<T*>(a.dP);
+  for (int idx = threadIdx.x; idx < UPB * SP * SP; idx += blockDim.x) {
+    const int u = idx / (SP * SP), e = idx % (SP * SP);
+    const int unit = unit0 + u;
+    if (unit >= n_units) continue;
+    const int s = e / SP, t = e % SP;
+    double acc = 0.0, dacc = 0.0;
+    if (s < S && t < S) {
+      for (int m = 0; m < S; ++m) {
+        const double vv = a.V[s * S + m] * a.Vinv[m * S + t];
+        acc = fma(vv, she[u][m], acc);
+        dacc = fma(vv, shd[u][m], dacc);
+      }
+    }
+    P[(size_t)unit * SP * SP + e] = (T)acc;
+    dP[(size_t)unit * SP * SP + e] = (T)dacc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Register kernels (SP <= 20): one thread per (pattern, category); the RP
+// lanes of a pattern are adjacent so the shared rescale is a shuffle.
+// ---------------------------------------------------------------------------
+
+// u = P_b v_b for child b of the current node (a tip's compact state picks a
+// column of P; the gap code gives the all-ones vector).  With dM != nullptr
+// also w = dP_b v_b.  Adds the child's cumulative exponent to e.
+template <typename T, int SP, bool WITH_D>
+__device__ __forceinline__ void child_up(const LevelArgs<T>& a, int b, int c,
+                                         int r, bool active,
+                                         const T* __restrict__ M,
+                                         const T* __restrict__ dM,
+                                         T (&u)[SP], T (&w)[SP], int& e) {
+  const int C = a.n_patterns;
+  if (b < a.n_tips && !(a.tip_has_partials && a.tip_has_partials[b])) {
+    const int y = active ? (int)a.tip_states[(size_t)b * C + c] : 0;
+    if (y < a.n_states) {
+#pragma unroll
+      for (int s = 0; s < SP; ++s) u[s] = M[s * SP + y];
+      if constexpr (WITH_D) {
+#pragma unroll
+        for (int s = 0; s < SP; ++s) w[s] = dM[s * SP + y];
+      }
+    } else {
+#pragma unroll
+      for (int s = 0; s < SP; ++s) u[s] = s < a.n_states ? T(1) : T(0);
+      if constexpr (WITH_D) {
+#pragma unroll
+        for (int s = 0; s < SP; ++s) w[s] = T(0);
+      }
+    }
+    return;
+  }
+  T v[SP];
+  if (b < a.n_tips) {
+    load_vec<T, SP>(a.tip_partials + ((size_t)b * C + c) * SP, v, active);
+  } else {
+    const size_t slot = (size_t)(b - a.n_tips);
+    load_vec<T, SP>(a.post + ((slot * C + c) * a.n_cat + r) * SP, v, active);
+    if (active) e += a.escale[slot * C + c];
+  }
+  matvec<T, SP>(M, v, u);
+  if constexpr (WITH_D) matvec<T, SP>(dM, v, w);
+}
+
+template <typename T, int SP, int RP>
+__device__ __forceinline__ void stage_mats(const T* __restrict__ src_base,
+                                           int b, int R, T* dst) {
+  constexpr int MS = MatStride<T, SP>::v;
+  const T* src = src_base + (size_t)b * R * SP * SP;
+  for (int idx = threadIdx.x; idx < R * SP * SP; idx += blockDim.x) {
+    const int rr = idx / (SP * SP), e = idx % (SP * SP);
+    dst[rr * MS + e] = src[idx];
+  }
+}
+
+// Post-order level (Eq. 2): p_k = (P_i p_i) o (P_j p_j), rescaled; at the
+// root also log P(Y_c) (Eq. 3) weighted by W_c and summed per tile.
+template <typename T, int SP, int RP>
+__global__ void __launch_bounds__(kSmallThreads)
+post_small_kernel(LevelArgs<T> a) {
+  constexpr int NT = kSmallThreads, CT = NT / RP;
+  constexpr int MS = MatStride<T, SP>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* smP[2];
+  smP[0] = reinterpret_cast<T*>(smraw);
+  smP[1] = smP[0] + RP * MS;
+  __shared__ double red[NT / 32][2];
+  const int k = a.level_nodes[blockIdx.y];
+  const int2 ch = a.children[k];
+  const int R = a.n_cat, C = a.n_patterns;
+  const int c = blockIdx.x * CT + threadIdx.x / RP;
+  const int r = threadIdx.x % RP;
+  const bool valid_c = c < C;
+  const bool active = valid_c && r < R;
+  stage_mats<T, SP, RP>(a.P, ch.x, R, smP[0]);
+  stage_mats<T, SP, RP>(a.P, ch.y, R, smP[1]);
+  __syncthreads();
+  const int rr = r < R ? r : 0;
+  T ui[SP], uj[SP], dummy[SP];
+  int e = 0;
+  child_up<T, SP, false>(a, ch.x, c, r, active, smP[0] + rr * MS, nullptr, ui,
+                         dummy, e);
+  child_up<T, SP, false>(a, ch.y, c, r, active, smP[1] + rr * MS, nullptr, uj,
+                         dummy, e);
+#pragma unroll
+  for (int s = 0; s < SP; ++s) ui[s] *= uj[s];
+  const T m = pattern_max<T, SP, RP>(ui, active);
+  e += rescale<T, SP>(ui, m, valid_c, a.err);
+  if (k != a.root) {
+    const size_t slot = (size_t)(k - a.n_tips);
+    if (active) {
+      store_vec<T, SP>(a.post + ((slot * C + c) * R + r) * SP, ui);
+      if (r == 0) a.escale[slot * C + c] = e;
+    }
+    return;
+  }
+  // Root: L_c = sum_r w_r pi' p_root (Eq. 3), with the exponents restored.
+  double lr = 0.0;
+  if (active) {
+#pragma unroll
+    for (int s = 0; s < SP; ++s)
+      if (s < a.n_states) lr += a.root_pi[s] * (double)ui[s];
+    lr *= a.cat_w[r];
+  }
+  lr = sum_over_lanes<RP>(lr);
+  double term = 0.0, unused = 0.0;
+  if (valid_c && r == 0) {
+    if (!(lr > 0.0) || !isfinite(lr)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+    term = a.pattern_w[c] * (log(lr) + (double)e * 0.69314718055994530942);
+  }
+  block_sum2<NT>(term, unused, red);
+  if (threadIdx.x == 0) a.lpart[blockIdx.x] = term;
+}
+
+// Pre-order level (Eq. 4) with the fused gradient (Eq. 8): for parent k,
+//   q_i = P_i' (q_k o P_j p_j),  q_j = P_j' (q_k o P_i p_i)
+// stored (rescaled) for internal children; the ratio for branches i and j
+// is reduced over the tile's patterns with weights W_c (Eq. 7).
+template <typename T, int SP, int RP>
+__global__ void __launch_bounds__(kSmallThreads)
+pre_small_kernel(LevelArgs<T> a) {
+  constexpr int NT = kSmallThreads, CT = NT / RP;
+  constexpr int MS = MatStride<T, SP>::v;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* smP[2];
+  T* smD[2];
+  smP[0] = reinterpret_cast<T*>(smraw);
+  smP[1] = smP[0] + RP * MS;
+  smD[0] = smP[1] + RP * MS;
+  smD[1] = smD[0] + RP * MS;
+  __shared__ double red[NT / 32][2];
+  const int k = a.level_nodes[blockIdx.y];
+  const int2 ch = a.children[k];
+  const int R = a.n_cat, C = a.n_patterns;
+  const int c = blockIdx.x * CT + threadIdx.x / RP;
+  const int r = threadIdx.x % RP;
+  const bool valid_c = c < C;
+  const bool active = valid_c && r < R;
+  stage_mats<T, SP, RP>(a.P, ch.x, R, smP[0]);
+  stage_mats<T, SP, RP>(a.P, ch.y, R, smP[1]);
+  stage_mats<T, SP, RP>(a.dP, ch.x, R, smD[0]);
+  stage_mats<T, SP, RP>(a.dP, ch.y, R, smD[1]);
+  __syncthreads();
+  const int rr = r < R ? r : 0;
+  T q[SP];
+  if (k == a.root) {
+#pragma unroll
+    for (int s = 0; s < SP; ++s)
+      q[s] = (active && s < a.n_states) ? (T)a.root_pi[s] : T(0);
+  } else {
+    const size_t slot = (size_t)(k - a.n_tips);
+    load_vec<T, SP>(a.pre + ((slot * C + c) * R + r) * SP, q, active);
+  }
+  T ui[SP], vi[SP], uj[SP], vj[SP];
+  int e_unused = 0;
+  child_up<T, SP, true>(a, ch.x, c, r, active, smP[0] + rr * MS,
+                        smD[0] + rr * MS, ui, vi, e_unused);
+  child_up<T, SP, true>(a, ch.y, c, r, active, smP[1] + rr * MS,
+                        smD[1] + rr * MS, uj, vj, e_unused);
+  // Per-category numerators and the shared denominator.
+  T num_i = T(0), num_j = T(0), den = T(0);
+#pragma unroll
+  for (int s = 0; s < SP; ++s) {
+    const T qi = q[s] * uj[s];  // a_i
+    const T qj = q[s] * ui[s];  // a_j
+    num_i = fma(qi, vi[s], num_i);
+    num_j = fma(qj, vj[s], num_j);
+    den = fma(qi, ui[s], den);
+  }
+  const double w = active ? a.cat_w[r] : 0.0;
+  double Ni = sum_over_lanes<RP>(w * (double)num_i);
+  double Nj = sum_over_lanes<RP>(w * (double)num_j);
+  const double D = sum_over_lanes<RP>(w * (double)den);
+  double gi = 0.0, gj = 0.0;
+  if (valid_c && r == 0) {
+    if (!(D > 0.0) || !isfinite(D)) {
+      atomicOr(a.err, ERR_BAD_RATIO);
+    } else {
+      const double W = a.pattern_w[c];
+      gi = W * (Ni / D);
+      gj = W * (Nj / D);
+    }
+  }
+  // Children's pre-order partials (internal children only).
+  if (ch.x >= a.n_tips) {
+    T av[SP], out[SP];
+#pragma unroll
+    for (int s = 0; s < SP; ++s) av[s] = q[s] * uj[s];
+    matvec_t<T, SP>(smP[0] + rr * MS, av, out);
+    const T m = pattern_max<T, SP, RP>(out, active);
+    rescale<T, SP>(out, m, valid_c, a.err);
+    if (active)
+      store_vec<T, SP>(
+          a.pre + (((size_t)(ch.x - a.n_tips) * C + c) * R + r) * SP, out);
+  }
+  if (ch.y >= a.n_tips) {
+    T av[SP], out[SP];
+#pragma unroll
+    for (int s = 0; s < SP; ++s) av[s] = q[s] * ui[s];
+    matvec_t<T, SP>(smP[1] + rr * MS, av, out);
+    const T m = pattern_max<T, SP, RP>(out, active);
+    rescale<T, SP>(out, m, valid_c, a.err);
+    if (active)
+      store_vec<T, SP>(
+          a.pre + (((size_t)(ch.y - a.n_tips) * C + c) * R + r) * SP, out);
+  }
+  block_sum2<NT>(gi, gj, red);
+  if (threadIdx.x == 0) {
+    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = gi;
+    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = gj;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory kernels for SP = 64 (S in 21..64): one thread per (pattern
+// group, state s); each thread owns CPG patterns of its group; categories
+// are processed one at a time with that category's matrices staged in a
+// padded (stride SP+1, bank-conflict-free both ways) shared layout.
+// ---------------------------------------------------------------------------
+template <typename T> struct WideCfg;
+template <> struct WideCfg<float> { static constexpr int CT = kWidePatternsF32; };
+template <> struct WideCfg<double> { static constexpr int CT = kWidePatternsF64; };
+
+constexpr int kWideSP = 64;
+constexpr int kWideLD = kWideSP + 1;
+
+template <typename T>
+__device__ __forceinline__ void stage_mat_padded(const T* __restrict__ src,
+                                                 T* dst) {
+  for (int idx = threadIdx.x; idx < kWideSP * kWideSP; idx += blockDim.x) {
+    const int s = idx / kWideSP, t = idx % kWideSP;
+    dst[s * kWideLD + t] = src[idx];
+  }
+}
+
+// Stage child vectors for category r into vin[CT][SP]; tips with compact
+// states store their state in ystate[CT] instead.
+template <typename T>
+__device__ __forceinline__ void stage_child_vec(const LevelArgs<T>& a, int b,
+                                                int c0, int r, T* vin,
+                                                int* ystate) {
+  constexpr int CT = WideCfg<T>::CT;
+  const int C = a.n_patterns, R = a.n_cat;
+  const bool compact =
+      b < a.n_tips && !(a.tip_has_partials && a.tip_has_partials[b]);
+  if (compact) {
+    for (int j = threadIdx.x; j < CT; j += blockDim.x) {
+      const int c = c0 + j;
+      ystate[j] = c < C ? (int)a.tip_states[(size_t)b * C + c] : 0;
+    }
+    return;
+  }
+  for (int idx = threadIdx.x; idx < CT * kWideSP; idx += blockDim.x) {
+    const int j = idx / kWideSP, s = idx % kWideSP, c = c0 + j;
+    T v = T(0);
+    if (c < C) {
+      if (b < a.n_tips)
+        v = a.tip_partials[((size_t)b * C + c) * kWideSP + s];
+      else
+        v = a.post[(((size_t)(b - a.n_tips) * C + c) * R + r) * kWideSP + s];
+    }
+    vin[j * kWideSP + s] = v;
+  }
+  if (threadIdx.x < CT) ystate[threadIdx.x] = -1;
+}
+
+// u = M v for state s of pattern j (M padded in smem).
+template <typename T>
+__device__ __forceinline__ T wide_up(const T* M, const T* vin, const int* ys,
+                                     int j, int s, int S) {
+  const int y = ys[j];
+  if (y >= 0) {
+    if (y < S) return M[s * kWideLD + y];
+    return s < S ? T(1) : T(0);
+  }
+  const T* v = vin + j * kWideSP;
+  T acc = T(0);
+#pragma unroll 16
+  for (int t = 0; t < kWideSP; ++t) acc = fma(M[s * kWideLD + t], v[t], acc);
+  return acc;
+}
+
+template <typename T>
+__device__ __forceinline__ T wide_up_gap_d(const int* ys, int j, int S,
+                                           T dval) {
+  // derivative of a gap tip's all-ones vector is exactly 0
+  const int y = ys[j];
+  return (y >= S) ? T(0) : dval;
+}
+
+template <typename T>
+struct WideSmemPost {
+  T mat[2][kWideSP * kWideLD];
+  T vin[2][WideCfg<T>::CT * kWideSP];
+  T pk[8][WideCfg<T>::CT * kWideSP];
+  int ys[2][WideCfg<T>::CT];
+  T redm[WideCfg<T>::CT][kWideThreads / 32];
+  double redl[kWideThreads / 32][2];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kWideThreads) post_wide_kernel(LevelArgs<T> a) {
+  constexpr int CT = WideCfg<T>::CT;
+  constexpr int NT = kWideThreads;
+  constexpr int GROUPS = NT / kWideSP;  // 4
+  constexpr int CPG = CT / GROUPS;      // patterns per thread
+  extern __shared__ __align__(16) unsigned char smraw[];
+  WideSmemPost<T>& sm = *reinterpret_cast<WideSmemPost<T>*>(smraw);
+  const int k = a.level_nodes[blockIdx.y];
+  const int2 ch = a.children[k];
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int c0 = blockIdx.x * CT;
+  const int g = threadIdx.x / kWideSP, s = threadIdx.x % kWideSP;
+  int eacc[CPG];
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) eacc[jj] = 0;
+  for (int r = 0; r < R; ++r) {
+    __syncthreads();
+    stage_mat_padded<T>(a.P + ((size_t)ch.x * R + r) * kWideSP * kWideSP,
+                        sm.mat[0]);
+    stage_mat_padded<T>(a.P + ((size_t)ch.y * R + r) * kWideSP * kWideSP,
+                        sm.mat[1]);
+    stage_child_vec<T>(a, ch.x, c0, r, sm.vin[0], sm.ys[0]);
+    stage_child_vec<T>(a, ch.y, c0, r, sm.vin[1], sm.ys[1]);
+    __syncthreads();
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) {
+      const int j = g * CPG + jj;
+      const T ui = wide_up<T>(sm.mat[0], sm.vin[0], sm.ys[0], j, s, S);
+      const T uj = wide_up<T>(sm.mat[1], sm.vin[1], sm.ys[1], j, s, S);
+      sm.pk[r][j * kWideSP + s] = ui * uj;
+    }
+  }
+  __syncthreads();
+  // exponents of the children (internal ones)
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj, c = c0 + j;
+    int e = 0;
+    if (c < C) {
+      if (ch.x >= a.n_tips) e += a.escale[(size_t)(ch.x - a.n_tips) * C + c];
+      if (ch.y >= a.n_tips) e += a.escale[(size_t)(ch.y - a.n_tips) * C + c];
+    }
+    eacc[jj] = e;
+  }
+  // max over (r, s) per pattern: 64 threads of the group = 2 warps
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj;
+    T m = T(0);
+    for (int r = 0; r < R; ++r) m = tmax(m, fabs(sm.pk[r][j * kWideSP + s]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = tmax(m, __shfl_xor_sync(kFull, m, o));
+    if ((threadIdx.x & 31) == 0) sm.redm[j][warp] = m;
+  }
+  __syncthreads();
+  double lterm = 0.0;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj, c = c0 + j;
+    const T m = tmax(sm.redm[j][2 * g], sm.redm[j][2 * g + 1]);
+    int e = 0;
+    if (c < C) {
+      if (!(m > T(0)) || !isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else (void)frexp(m, &e);
+    }
+    const T f = ldexp(T(1), -e);
+    const int etot = e + eacc[jj];
+    if (k != a.root) {
+      if (c < C) {
+        const size_t slot = (size_t)(k - a.n_tips);
+        for (int r = 0; r < R; ++r)
+          a.post[((slot * C + c) * R + r) * kWideSP + s] =
+              sm.pk[r][j * kWideSP + s] * f;
+        if (s == 0) a.escale[slot * C + c] = etot;
+      }
+    } else {
+      // root: sum_r w_r pi' p over the group's 64 threads
+      double lr = 0.0;
+      if (c < C && s < S)
+        for (int r = 0; r < R; ++r)
+          lr += a.cat_w[r] * a.root_pi[s] *
+                (double)(sm.pk[r][j * kWideSP + s] * f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lr += __shfl_xor_sync(kFull, lr, o);
+      // combine the group's two warps through shared memory
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) sm.redl[warp][0] = lr;
+      __syncthreads();
+      if (s == 0 && c < C) {
+        const double L = sm.redl[2 * g][0] + sm.redl[2 * g + 1][0];
+        if (!(L > 0.0) || !isfinite(L)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+        lterm += a.pattern_w[c] * (log(L) + (double)etot * 0.69314718055994530942);
+      }
+    }
+  }
+  if (k == a.root) {
+    __syncthreads();
+    double unused = 0.0;
+    block_sum2<NT>(lterm, unused, sm.redl);
+    if (threadIdx.x == 0) a.lpart[blockIdx.x] = lterm;
+  }
+}
+
+template <typename T>
+struct WideSmemPre {
+  T mat[4][kWideSP * kWideLD];   // P_i, P_j, dP_i, dP_j for one r
+  T vin[2][WideCfg<T>::CT * kWideSP];
+  T qk[WideCfg<T>::CT * kWideSP];
+  T av[2][WideCfg<T>::CT * kWideSP];
+  int ys[2][WideCfg<T>::CT];
+  T redm[2][WideCfg<T>::CT][kWideThreads / 32];
+  double red[kWideThreads / 32][2];
+  double redg[3][WideCfg<T>::CT][kWideThreads / 32];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) {
+  constexpr int CT = WideCfg<T>::CT;
+  constexpr int NT = kWideThreads;
+  constexpr int GROUPS = NT / kWideSP;
+  constexpr int CPG = CT / GROUPS;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  WideSmemPre<T>& sm = *reinterpret_cast<WideSmemPre<T>*>(smraw);
+  T* qout = reinterpret_cast<T*>(smraw + sizeof(WideSmemPre<T>));  // [2][R][CT][SP]
+  const int k = a.level_nodes[blockIdx.y];
+  const int2 ch = a.children[k];
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int c0 = blockIdx.x * CT;
+  const int g = threadIdx.x / kWideSP, s = threadIdx.x % kWideSP;
+  const bool int_i = ch.x >= a.n_tips, int_j = ch.y >= a.n_tips;
+  double ni[CPG], nj[CPG], dd[CPG];
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) { ni[jj] = 0.0; nj[jj] = 0.0; dd[jj] = 0.0; }
+  for (int r = 0; r < R; ++r) {
+    __syncthreads();
+    stage_mat_padded<T>(a.P + ((size_t)ch.x * R + r) * kWideSP * kWideSP, sm.mat[0]);
+    stage_mat_padded<T>(a.P + ((size_t)ch.y * R + r) * kWideSP * kWideSP, sm.mat[1]);
+    stage_mat_padded<T>(a.dP + ((size_t)ch.x * R + r) * kWideSP * kWideSP, sm.mat[2]);
+    stage_mat_padded<T>(a.dP + ((size_t)ch.y * R + r) * kWideSP * kWideSP, sm.mat[3]);
+    stage_child_vec<T>(a, ch.x, c0, r, sm.vin[0], sm.ys[0]);
+    stage_child_vec<T>(a, ch.y, c0, r, sm.vin[1], sm.ys[1]);
+    for (int idx = threadIdx.x; idx < CT * kWideSP; idx += NT) {
+      const int j = idx / kWideSP, ss = idx % kWideSP, c = c0 + j;
+      T v = T(0);
+      if (c < C) {
+        if (k == a.root) v = ss < S ? (T)a.root_pi[ss] : T(0);
+        else v = a.pre[(((size_t)(k - a.n_tips) * C + c) * R + r) * kWideSP + ss];
+      }
+      sm.qk[idx] = v;
+    }
+    __syncthreads();
+    const double wr = a.cat_w[r];
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) {
+      const int j = g * CPG + jj;
+      const T ui = wide_up<T>(sm.mat[0], sm.vin[0], sm.ys[0], j, s, S);
+      const T uj = wide_up<T>(sm.mat[1], sm.vin[1], sm.ys[1], j, s, S);
+      const T vi = wide_up_gap_d<T>(sm.ys[0], j, S,
+                                   wide_up<T>(sm.mat[2], sm.vin[0], sm.ys[0], j, s, S));
+      const T vj = wide_up_gap_d<T>(sm.ys[1], j, S,
+                                   wide_up<T>(sm.mat[3], sm.vin[1], sm.ys[1], j, s, S));
+      const T q = sm.qk[j * kWideSP + s];
+      const T ai = q * uj, aj = q * ui;
+      ni[jj] += wr * (double)(ai * vi);
+      nj[jj] += wr * (double)(aj * vj);
+      dd[jj] += wr * (double)(ai * ui);
+      sm.av[0][j * kWideSP + s] = ai;
+      sm.av[1][j * kWideSP + s] = aj;
+    }
+    __syncthreads();
+    // q_child[t = s] = sum_s' P[s'][t] a[s'] for this r (unscaled)
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) {
+      const int j = g * CPG + jj;
+      for (int x = 0; x < 2; ++x) {
+        if (!(x == 0 ? int_i : int_j)) continue;
+        const T* M = sm.mat[x];
+        const T* av = sm.av[x] + j * kWideSP;
+        T acc = T(0);
+#pragma unroll 16
+        for (int sp = 0; sp < kWideSP; ++sp) acc = fma(M[sp * kWideLD + s], av[sp], acc);
+        qout[((x * R + r) * CT + j) * kWideSP + s] = acc;
+      }
+    }
+  }
+  // Gradient ratio per pattern: reduce ni, nj, dd over the group's 64 states.
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj;
+    double x0 = ni[jj], x1 = nj[jj], x2 = dd[jj];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      x0 += __shfl_xor_sync(kFull, x0, o);
+      x1 += __shfl_xor_sync(kFull, x1, o);
+      x2 += __shfl_xor_sync(kFull, x2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      sm.redg[0][j][warp] = x0; sm.redg[1][j][warp] = x1; sm.redg[2][j][warp] = x2;
+    }
+  }
+  // Max of each child's unscaled q over (r, s) per pattern.
+  __syncthreads();
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj;
+    for (int x = 0; x < 2; ++x) {
+      T m = T(0);
+      if (x == 0 ? int_i : int_j)
+        for (int r = 0; r < R; ++r)
+          m = tmax(m, fabs(qout[((x * R + r) * CT + j) * kWideSP + s]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = tmax(m, __shfl_xor_sync(kFull, m, o));
+      if ((threadIdx.x & 31) == 0) sm.redm[x][j][warp] = m;
+    }
+  }
+  __syncthreads();
+  double gi = 0.0, gj = 0.0;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj, c = c0 + j;
+    if (c >= C) continue;
+    if (s == 0) {
+      const double Ni = sm.redg[0][j][2 * g] + sm.redg[0][j][2 * g + 1];
+      const double Nj = sm.redg[1][j][2 * g] + sm.redg[1][j][2 * g + 1];
+      const double D = sm.redg[2][j][2 * g] + sm.redg[2][j][2 * g + 1];
+      if (!(D > 0.0) || !isfinite(D)) {
+        atomicOr(a.err, ERR_BAD_RATIO);
+      } else {
+        gi += a.pattern_w[c] * (Ni / D);
+        gj += a.pattern_w[c] * (Nj / D);
+      }
+    }
+    for (int x = 0; x < 2; ++x) {
+      const int b = x == 0 ? ch.x : ch.y;
+      if (b < a.n_tips) continue;
+      const T m = tmax(sm.redm[x][j][2 * g], sm.redm[x][j][2 * g + 1]);
+      int e = 0;
+      if (!(m > T(0)) || !isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else (void)frexp(m, &e);
+      const T f = ldexp(T(1), -e);
+      const size_t slot = (size_t)(b - a.n_tips);
+      for (int r = 0; r < R; ++r)
+        a.pre[((slot * C + c) * R + r) * kWideSP + s] =
+            qout[((x * R + r) * CT + j) * kWideSP + s] * f;
+    }
+  }
+  __syncthreads();
+  block_sum2<NT>(gi, gj, sm.red);
+  if (threadIdx.x == 0) {
+    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = gi;
+    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = gj;
+  }
+}
+
+template <typename T>
+inline size_t wide_post_smem() { return sizeof(WideSmemPost<T>); }
+template <typename T>
+inline size_t wide_pre_smem(int R) {
+  return sizeof(WideSmemPre<T>) +
+         (size_t)2 * R * WideCfg<T>::CT * kWideSP * sizeof(T);
+}
+
+// ---------------------------------------------------------------------------
+// Instantiation of the launchers for one element type.
+// ---------------------------------------------------------------------------
+template <typename T, int SP, int RP>
+constexpr size_t small_smem(bool post) {
+  return (size_t)(post ? 2 : 4) * RP * MatStride<T, SP>::v * sizeof(T);
+}
+
+template <typename T, int SP, int RP>
+cudaError_t launch_small(const LevelArgs<T>& a, bool post, cudaStream_t st) {
+  dim3 grid(a.n_tiles, a.n_level);
+  if (post)
+    post_small_kernel<T, SP, RP>
+        <<<grid, kSmallThreads, small_smem<T, SP, RP>(true), st>>>(a);
+  else
+    pre_small_kernel<T, SP, RP>
+        <<<grid, kSmallThreads, small_smem<T, SP, RP>(false), st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, int SP, int RP>
+cudaError_t prepare_small() {
+  cudaError_t e = cudaFuncSetAttribute(
+      post_small_kernel<T, SP, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)small_smem<T, SP, RP>(true));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(pre_small_kernel<T, SP, RP>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)small_smem<T, SP, RP>(false));
+}
+
+template <typename T, int SP>
+cudaError_t prepare_small_rp(int RP) {
+  switch (RP) {
+    case 1: return prepare_small<T, SP, 1>();
+    case 2: return prepare_small<T, SP, 2>();
+    case 4: return prepare_small<T, SP, 4>();
+    case 8: return prepare_small<T, SP, 8>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int SP>
+cudaError_t launch_small_rp(const LevelArgs<T>& a, int RP, bool post,
+                            cudaStream_t st) {
+  switch (RP) {
+    case 1: return launch_small<T, SP, 1>(a, post, st);
+    case 2: return launch_small<T, SP, 2>(a, post, st);
+    case 4: return launch_small<T, SP, 4>(a, post, st);
+    case 8: return launch_small<T, SP, 8>(a, post, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t launch_level_impl(const LevelArgs<T>& a, int SP, int RP, bool post,
+                              cudaStream_t st) {
+  if (a.n_tiles <= 0 || a.n_level <= 0) return cudaSuccess;
+  switch (SP) {
+    case 4: return launch_small_rp<T, 4>(a, RP, post, st);
+    case 20: return launch_small_rp<T, 20>(a, RP, post, st);
+    case 64: {
+      dim3 grid(a.n_tiles, a.n_level);
+      if (post)
+        post_wide_kernel<T><<<grid, kWideThreads, wide_post_smem<T>(), st>>>(a);
+      else
+        pre_wide_kernel<T><<<grid, kWideThreads, wide_pre_smem<T>(a.n_cat), st>>>(a);
+      return cudaGetLastError();
+    }
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+cudaError_t prepare_impl(int SP, int RP) {
+  if (SP == 4) return prepare_small_rp<T, 4>(RP);
+  if (SP == 20) return prepare_small_rp<T, 20>(RP);
+  if (SP == 64) {
+    cudaError_t e = cudaFuncSetAttribute(
+        post_wide_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)wide_post_smem<T>());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pre_wide_kernel<T>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)wide_pre_smem<T>(8));
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
+  const int units = a.n_branches * a.n_cat;
+  if (units <= 0) return cudaSuccess;
+  switch (SP) {
+    case 4: {
+      constexpr int UPB = 256 / 16;
+      pmat_kernel<T, 4><<<(units + UPB - 1) / UPB, 256, 0, st>>>(a);
+      break;
+    }
+    case 20: pmat_kernel<T, 20><<<units, 256, 0, st>>>(a); break;
+    case 64: pmat_kernel<T, 64><<<units, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace phylo
+
+#define PHYLO_INSTANTIATE(T)                                                  \
+  namespace phylo {                                                           \
+  template <>                                                                 \
+  cudaError_t launch_pmat<T>(const PmatArgs& a, int SP, cudaStream_t st) {    \
+    return launch_pmat_impl<T>(a, SP, st);                                    \
+  }                                                                           \
+  template <>                                                                 \
+  cudaError_t launch_post_level<T>(const LevelArgs<T>& a, int SP, int RP,     \
+                                   cudaStream_t st) {                         \
+    return launch_level_impl<T>(a, SP, RP, true, st);                         \
+  }                                                                           \
+  template <>                                                                 \
+  cudaError_t launch_pre_level<T>(const LevelArgs<T>& a, int SP, int RP,      \
+                                  cudaStream_t st) {                          \
+    return launch_level_impl<T>(a, SP, RP, false, st);                        \
+  }                                                                           \
+  template <>                                                                 \
+  cudaError_t prepare_kernels<T>(int SP, int RP) {                            \
+    return prepare_impl<T>(SP, RP);                                           \
+  }                                                                           \
+  }

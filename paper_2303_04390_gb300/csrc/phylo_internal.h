@@ -1,0 +1,104 @@
+// Internal declarations shared by the host API (phylo_api.cu) and the kernel
+// translation units (kernels_fp32.cu, kernels_fp64.cu).  Not installed.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace phylo {
+
+// Device-side numeric flags (bit mask in the workspace's error word).
+enum : int {
+  ERR_ZERO_PARTIAL = 1,  // a partial vector was all zero / NaN for a pattern
+  ERR_BAD_LENGTH = 2,    // a branch length was negative or not finite
+  ERR_BAD_RATIO = 4      // a gradient denominator was zero or not finite
+};
+
+// Padded state count used by the kernels for a model with S states.
+inline int padded_states(int S) {
+  if (S <= 4) return 4;
+  if (S <= 20) return 20;
+  return 64;
+}
+
+// Lanes per pattern in the register kernels (next power of two >= R).
+inline int lanes_per_pattern(int R) {
+  int rp = 1;
+  while (rp < R) rp <<= 1;
+  return rp;
+}
+
+// Threads per block of the register kernels (one thread per (pattern, r)).
+constexpr int kSmallThreads = 128;
+// Patterns per block of the shared-memory kernels for S_pad = 64.
+constexpr int kWideThreads = 256;
+constexpr int kWidePatternsF32 = 16;
+constexpr int kWidePatternsF64 = 8;
+
+// Patterns handled by one thread block of a level kernel.
+inline int patterns_per_tile(int SP, int R, bool fp64) {
+  if (SP <= 20) return kSmallThreads / lanes_per_pattern(R);
+  return fp64 ? kWidePatternsF64 : kWidePatternsF32;
+}
+
+// Arguments of the post- and pre-order level kernels.  All arrays live in
+// the caller's workspace.  Partials are pattern-major: [slot][c][r][SP],
+// slot = node - n_tips for internal nodes.
+template <typename T>
+struct LevelArgs {
+  const int2* children;        // [2N-1]; (-1,-1) for tips
+  const int* level_nodes;      // internal nodes of this level
+  int n_level;                 // number of nodes in the level
+  int n_tips, n_patterns, n_states, n_cat, root;
+  const T* P;                  // [2N-2][R][SP][SP], row = parent state
+  const T* dP;                 // same layout: dP/dt = gamma_r Q P
+  T* post;                     // [N-1][C][R][SP] post-order partials
+  T* pre;                      // [N-1][C][R][SP] pre-order partials
+  int* escale;                 // [N-1][C] cumulative post-order exponents
+  const uint8_t* tip_states;   // [N][C]; value S = gap
+  const T* tip_partials;       // [N][C][SP] or nullptr
+  const int* tip_has_partials; // [N] or nullptr
+  const double* pattern_w;     // [C]
+  const double* root_pi;       // [S]
+  const double* cat_w;         // [R]
+  double* gpart;               // [2N-2][n_tiles] per-tile gradient sums
+  double* lpart;               // [n_tiles] per-tile log-likelihood sums
+  int n_tiles;
+  int* err;                    // numeric flags
+};
+
+struct PmatArgs {
+  const double* V;       // [S][S]
+  const double* Vinv;    // [S][S]
+  const double* lambda;  // [S]
+  const double* rates;   // [R]
+  const double* t;       // [n_branches]
+  int n_branches, n_states, n_cat;
+  void* P;               // [n_branches][R][SP][SP] of T
+  void* dP;
+  int* err;
+};
+
+struct ReduceArgs {
+  const double* gpart;   // [n_branches][n_tiles]
+  const double* lpart;   // [n_tiles]
+  int n_tiles, n_branches;
+  double* out;           // [1 + n_branches]
+};
+
+// Launchers (kernels_fp32.cu / kernels_fp64.cu).  SP = padded states.
+template <typename T>
+cudaError_t launch_pmat(const PmatArgs& a, int SP, cudaStream_t st);
+template <typename T>
+cudaError_t launch_post_level(const LevelArgs<T>& a, int SP, int RP,
+                              cudaStream_t st);
+template <typename T>
+cudaError_t launch_pre_level(const LevelArgs<T>& a, int SP, int RP,
+                             cudaStream_t st);
+template <typename T>
+cudaError_t prepare_kernels(int SP, int RP);
+cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
+
+}  // namespace phylo

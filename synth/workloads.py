@@ -10,7 +10,7 @@ The paper's datasets (dengue, carnivores, yeast, West Nile virus; Results
 section) are not available, so every workload here is synthetic: Yule trees
 with i.i.d. exponential branch lengths and alignments simulated along them.
 
-Conventions (paper, Section 2): tips are nodes 0..N-1, internal nodes
+Conventions (paper, Methods): tips are nodes 0..N-1, internal nodes
 N..2N-2 numbered in post-order, the root is node 2N-2, and branch i is the
 branch above node i. ``parent[root] == -1``.
 
@@ -121,7 +121,7 @@ def exponential_branch_lengths(n_tips: int, mean: float,
 # ---------------------------------------------------------------------------
 # Substitution models: every Q is reversible w.r.t. pi and scaled to mean
 # rate 1 (-sum_i pi_i Q_ii = 1), so branch lengths are expected numbers of
-# substitutions per site (paper, Section 2).
+# substitutions per site (paper, Methods).
 # ---------------------------------------------------------------------------
 
 
