@@ -294,6 +294,43 @@ def evaluate(parent, t, Q, pi, rates, weights, pattern_weights,
     return logL, grad, abs_sum
 
 
+def gradient_numerator_abs(p_i, Q, q_i, rates):
+    """gamma_r |p_i|' |Q|' |q_i| for every r, c: the numerator of Eq. 8
+    with every term taken in absolute value (its rounding-error scale)."""
+    return np.asarray(rates)[:, None] * np.einsum(
+        "rcs,us,rcu->rc", np.abs(p_i), np.abs(Q), np.abs(q_i))
+
+
+def evaluate_with_scales(parent, t, Q, pi, rates, weights, pattern_weights,
+                         tip_states=None, tip_partials=None):
+    """evaluate() plus the conditioning scale of every gradient entry:
+
+    returns (logL, grad, A, B) with
+      A_i = sum_c W_c |g_ic|                       (cross-pattern cancellation)
+      B_i = sum_c W_c sum_r w_r |Eq. 8 numerator terms| / den_c
+                                        (cross-pattern and within-pattern)
+    B_i >= A_i.  A finite-precision evaluation of entry i carries an error
+    proportional to B_i, not to |grad_i|.
+    """
+    logL, grad, A, det = evaluate(parent, t, Q, pi, rates, weights,
+                                  pattern_weights, tip_states=tip_states,
+                                  tip_partials=tip_partials,
+                                  return_details=True)
+    Qa = np.asarray(Q, dtype=np.float64)
+    wts = np.asarray(weights, dtype=np.float64)
+    W = np.asarray(pattern_weights, dtype=np.float64)
+    B = np.zeros_like(A)
+    for i in range(len(parent)):
+        if i == det["root"]:
+            continue
+        p_i, q_i = det["p"][i], det["q"][i]
+        num = np.einsum("rc,r->c", gradient_numerator_abs(p_i, Qa, q_i, rates),
+                        wts)
+        den = np.einsum("rc,r->c", node_likelihood_terms(p_i, q_i), wts)
+        B[i] = float(np.dot(W, num / den))
+    return logL, grad, A, B
+
+
 def node_site_log_likelihoods(details, weights, node):
     """log sum_r w_r p_i' q_i for every c at ``node`` (Eq. 5); equals the
     site log-likelihood at every node."""

@@ -138,11 +138,83 @@ __device__ __forceinline__ int rescale(T (&v)[SP], T m, bool valid_pattern,
   return e;
 }
 
-template <int RP>
-__device__ __forceinline__ double sum_over_lanes(double x) {
+template <int RP, typename X>
+__device__ __forceinline__ X sum_over_lanes(X x) {
 #pragma unroll
   for (int o = 1; o < RP; o <<= 1) x += __shfl_xor_sync(kFull, x, o);
   return x;
+}
+
+// Cross-pattern accumulator.  FP64 path: double.  FP32 path: an unevaluated
+// pair hi + lo of floats kept exact with error-free transformations
+// (Knuth's TwoSum, and TwoProd via fma), i.e. ~48-bit sums without FP64
+// arithmetic, whose throughput on this part is a small fraction of FP32's.
+// The pair is converted to FP64 once per tile; tiles are summed in FP64.
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+  F2 s = two_sum(x.hi, y.hi);
+  const float lo = s.lo + (x.lo + y.lo);
+  const float hi = s.hi + lo;
+  return {hi, lo - (hi - s.hi)};
+}
+
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  using type = double;
+  __device__ static double zero() { return 0.0; }
+  __device__ static double prod(double w, double g) { return w * g; }
+  __device__ static double add(double a, double b) { return a + b; }
+  __device__ static double shfl_down(double a, int o) {
+    return __shfl_down_sync(kFull, a, o);
+  }
+  __device__ static double to_double(double a) { return a; }
+};
+template <> struct Acc<float> {
+  using type = F2;
+  __device__ static F2 zero() { return {0.f, 0.f}; }
+  __device__ static F2 prod(double w, float g) {
+    const float wf = (float)w;
+    const float p = wf * g;
+    return {p, fmaf(wf, g, -p)};
+  }
+  __device__ static F2 add(F2 a, F2 b) { return f2_add(a, b); }
+  __device__ static F2 shfl_down(F2 a, int o) {
+    return {__shfl_down_sync(kFull, a.hi, o), __shfl_down_sync(kFull, a.lo, o)};
+  }
+  __device__ static double to_double(F2 a) { return (double)a.hi + (double)a.lo; }
+};
+
+// Block-wide sum of two accumulators; the result is valid in thread 0.
+// Lanes below `first` never hold values, so the first shuffle distance is
+// `first` (a power of two).
+template <typename T, int NT>
+__device__ __forceinline__ void block_sum_acc(typename Acc<T>::type& a,
+                                              typename Acc<T>::type& b,
+                                              typename Acc<T>::type (*sm)[2],
+                                              int first) {
+  using A = Acc<T>;
+  for (int o = 16; o >= first; o >>= 1) {
+    a = A::add(a, A::shfl_down(a, o));
+    b = A::add(b, A::shfl_down(b, o));
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { sm[w][0] = a; sm[w][1] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = sm[0][0]; b = sm[0][1];
+#pragma unroll
+    for (int i = 1; i < NT / 32; ++i) { a = A::add(a, sm[i][0]); b = A::add(b, sm[i][1]); }
+  }
 }
 
 // Block-wide sum of one or two doubles (fixed order: deterministic).
@@ -168,7 +240,10 @@ __device__ __forceinline__ void block_sum2(double& a, double& b,
 // Eq. 1: P^(r)(t_b) = V diag(e^{lambda gamma_r t_b}) Vinv and
 //        dP/dt       = V diag(gamma_r lambda e^{lambda gamma_r t_b}) Vinv,
 // for every (branch, category) in one launch, computed in FP64 and stored
-// as T with zero padding.
+// as T with zero padding.  P is formed as I + V diag(expm1(.)) Vinv: the
+// direct form cancels catastrophically in the off-diagonal entries of short
+// branches (relative error ~ u |V||Vinv| / (gamma t |Q|)), and at t = 0 it
+// gives P = I exactly.
 // ---------------------------------------------------------------------------
 template <typename T, int SP>
 __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
@@ -189,8 +264,9 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
         t = 0.0;
       }
       const double g = a.rates[r];
-      e = exp(a.lambda[m] * g * t);
-      de = g * a.lambda[m] * e;
+      const double x = a.lambda[m] * g * t;
+      e = expm1(x);                    // e^x - 1: no cancellation for small t
+      de = g * a.lambda[m] * exp(x);
     }
     she[u][m] = e;
     shd[u][m] = de;
@@ -210,6 +286,7 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
         acc = fma(vv, she[u][m], acc);
         dacc = fma(vv, shd[u][m], dacc);
       }
+      if (s == t) acc += 1.0;  // P = I + V diag(e^x - 1) Vinv
     }
     P[(size_t)unit * SP * SP + e] = (T)acc;
     dP[(size_t)unit * SP * SP + e] = (T)dacc;
@@ -348,7 +425,7 @@ pre_small_kernel(LevelArgs<T> a) {
   smP[1] = smP[0] + RP * MS;
   smD[0] = smP[1] + RP * MS;
   smD[1] = smD[0] + RP * MS;
-  __shared__ double red[NT / 32][2];
+  __shared__ typename Acc<T>::type red[NT / 32][2];
   const int k = a.level_nodes[blockIdx.y];
   const int2 ch = a.children[k];
   const int R = a.n_cat, C = a.n_patterns;
@@ -387,18 +464,20 @@ pre_small_kernel(LevelArgs<T> a) {
     num_j = fma(qj, vj[s], num_j);
     den = fma(qi, ui[s], den);
   }
-  const double w = active ? a.cat_w[r] : 0.0;
-  double Ni = sum_over_lanes<RP>(w * (double)num_i);
-  double Nj = sum_over_lanes<RP>(w * (double)num_j);
-  const double D = sum_over_lanes<RP>(w * (double)den);
-  double gi = 0.0, gj = 0.0;
+  // sum over categories (Eq. 8) in T, then the ratio in T
+  const T w = active ? (T)a.cat_w[r] : T(0);
+  const T Ni = sum_over_lanes<RP>(w * num_i);
+  const T Nj = sum_over_lanes<RP>(w * num_j);
+  const T D = sum_over_lanes<RP>(w * den);
+  using A = Acc<T>;
+  typename A::type gi = A::zero(), gj = A::zero();
   if (valid_c && r == 0) {
-    if (!(D > 0.0) || !isfinite(D)) {
+    if (!(D > T(0)) || !isfinite(D)) {
       atomicOr(a.err, ERR_BAD_RATIO);
     } else {
       const double W = a.pattern_w[c];
-      gi = W * (Ni / D);
-      gj = W * (Nj / D);
+      gi = A::prod(W, Ni / D);
+      gj = A::prod(W, Nj / D);
     }
   }
   // Children's pre-order partials (internal children only).
@@ -424,10 +503,10 @@ pre_small_kernel(LevelArgs<T> a) {
       store_vec<T, SP>(
           a.pre + (((size_t)(ch.y - a.n_tips) * C + c) * R + r) * SP, out);
   }
-  block_sum2<NT>(gi, gj, red);
+  block_sum_acc<T, NT>(gi, gj, red, RP);
   if (threadIdx.x == 0) {
-    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = gi;
-    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = gj;
+    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = A::to_double(gi);
+    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = A::to_double(gj);
   }
 }
 
@@ -630,8 +709,8 @@ struct WideSmemPre {
   T av[2][WideCfg<T>::CT * kWideSP];
   int ys[2][WideCfg<T>::CT];
   T redm[2][WideCfg<T>::CT][kWideThreads / 32];
-  double red[kWideThreads / 32][2];
-  double redg[3][WideCfg<T>::CT][kWideThreads / 32];
+  typename Acc<T>::type red[kWideThreads / 32][2];
+  T redg[3][WideCfg<T>::CT][kWideThreads / 32];
 };
 
 template <typename T>
@@ -649,9 +728,9 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
   const int c0 = blockIdx.x * CT;
   const int g = threadIdx.x / kWideSP, s = threadIdx.x % kWideSP;
   const bool int_i = ch.x >= a.n_tips, int_j = ch.y >= a.n_tips;
-  double ni[CPG], nj[CPG], dd[CPG];
+  T ni[CPG], nj[CPG], dd[CPG];
 #pragma unroll
-  for (int jj = 0; jj < CPG; ++jj) { ni[jj] = 0.0; nj[jj] = 0.0; dd[jj] = 0.0; }
+  for (int jj = 0; jj < CPG; ++jj) { ni[jj] = T(0); nj[jj] = T(0); dd[jj] = T(0); }
   for (int r = 0; r < R; ++r) {
     __syncthreads();
     stage_mat_padded<T>(a.P + ((size_t)ch.x * R + r) * kWideSP * kWideSP, sm.mat[0]);
@@ -670,7 +749,7 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
       sm.qk[idx] = v;
     }
     __syncthreads();
-    const double wr = a.cat_w[r];
+    const T wr = (T)a.cat_w[r];
 #pragma unroll
     for (int jj = 0; jj < CPG; ++jj) {
       const int j = g * CPG + jj;
@@ -682,9 +761,9 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
                                    wide_up<T>(sm.mat[3], sm.vin[1], sm.ys[1], j, s, S));
       const T q = sm.qk[j * kWideSP + s];
       const T ai = q * uj, aj = q * ui;
-      ni[jj] += wr * (double)(ai * vi);
-      nj[jj] += wr * (double)(aj * vj);
-      dd[jj] += wr * (double)(ai * ui);
+      ni[jj] = fma(wr, ai * vi, ni[jj]);
+      nj[jj] = fma(wr, aj * vj, nj[jj]);
+      dd[jj] = fma(wr, ai * ui, dd[jj]);
       sm.av[0][j * kWideSP + s] = ai;
       sm.av[1][j * kWideSP + s] = aj;
     }
@@ -709,7 +788,7 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
 #pragma unroll
   for (int jj = 0; jj < CPG; ++jj) {
     const int j = g * CPG + jj;
-    double x0 = ni[jj], x1 = nj[jj], x2 = dd[jj];
+    T x0 = ni[jj], x1 = nj[jj], x2 = dd[jj];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       x0 += __shfl_xor_sync(kFull, x0, o);
@@ -736,20 +815,21 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
     }
   }
   __syncthreads();
-  double gi = 0.0, gj = 0.0;
+  using A = Acc<T>;
+  typename A::type gi = A::zero(), gj = A::zero();
 #pragma unroll
   for (int jj = 0; jj < CPG; ++jj) {
     const int j = g * CPG + jj, c = c0 + j;
     if (c >= C) continue;
     if (s == 0) {
-      const double Ni = sm.redg[0][j][2 * g] + sm.redg[0][j][2 * g + 1];
-      const double Nj = sm.redg[1][j][2 * g] + sm.redg[1][j][2 * g + 1];
-      const double D = sm.redg[2][j][2 * g] + sm.redg[2][j][2 * g + 1];
-      if (!(D > 0.0) || !isfinite(D)) {
+      const T Ni = sm.redg[0][j][2 * g] + sm.redg[0][j][2 * g + 1];
+      const T Nj = sm.redg[1][j][2 * g] + sm.redg[1][j][2 * g + 1];
+      const T D = sm.redg[2][j][2 * g] + sm.redg[2][j][2 * g + 1];
+      if (!(D > T(0)) || !isfinite(D)) {
         atomicOr(a.err, ERR_BAD_RATIO);
       } else {
-        gi += a.pattern_w[c] * (Ni / D);
-        gj += a.pattern_w[c] * (Nj / D);
+        gi = A::add(gi, A::prod(a.pattern_w[c], Ni / D));
+        gj = A::add(gj, A::prod(a.pattern_w[c], Nj / D));
       }
     }
     for (int x = 0; x < 2; ++x) {
@@ -767,10 +847,10 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
     }
   }
   __syncthreads();
-  block_sum2<NT>(gi, gj, sm.red);
+  block_sum_acc<T, NT>(gi, gj, sm.red, 1);
   if (threadIdx.x == 0) {
-    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = gi;
-    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = gj;
+    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = A::to_double(gi);
+    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = A::to_double(gj);
   }
 }
 

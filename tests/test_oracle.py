@@ -428,3 +428,15 @@ def test_planted_transposed_postorder_matrix_is_caught():
     bf = O.brute_force_site_likelihoods(w.parent, w.t, w.Q, w.pi, w.rates,
                                         w.weights, tip_states=w.tip_states)
     assert not np.allclose(np.exp(ll), bf, rtol=1e-6)
+
+
+def test_conditioning_scales():
+    """The conditioning scales bound the entries: B_i >= A_i >= |grad_i|."""
+    w = synth.small_workload(9, 4, 4, 30, seed=18)
+    ll, g, A, B = O.evaluate_with_scales(w.parent, w.t, w.Q, w.pi, w.rates,
+                                         w.weights, w.pattern_weights,
+                                         tip_states=w.tip_states)
+    ll2, g2, A2 = O.evaluate(w.parent, w.t, w.Q, w.pi, w.rates, w.weights,
+                             w.pattern_weights, tip_states=w.tip_states)
+    assert ll == ll2 and np.array_equal(g, g2) and np.array_equal(A, A2)
+    assert np.all(B >= A * (1 - 1e-12)) and np.all(A >= np.abs(g) * (1 - 1e-12))

@@ -232,5 +232,5 @@ def test_full_size_workloads(name):
         root = 2 * w.n_tips - 2
         a, b = np.nonzero(w.parent == root)[0]
         assert abs(grad[a] - grad[b]) <= 2 * max(
-            TOL[prec]["g_rel"] * abs(ref[1][a]), TOL[prec]["g_cond"] * ref[2][a])
+            TOL[prec]["g_rel"] * abs(ref[1][a]), TOL[prec]["g_cond"] * ref[3][a])
         ctx.close()
