@@ -167,6 +167,48 @@ int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
  * when ctx is NULL).  Valid until the next call on ctx. */
 const char* phylo_last_error(const phylo_ctx* ctx);
 
+/* No-allocation evaluation (the paper has no counterpart: it exists for
+ * callers that cannot allocate device memory -- code that runs while a
+ * stream capture is active in global mode, where cudaMalloc is illegal;
+ * runtimes that own all device memory through their own pools; fixed-
+ * footprint samplers that must not grow after start-up).
+ *
+ * One FP32 evaluation of log P(Y) and its gradient, as phylo_evaluate,
+ * from host inputs to host outputs, without a context or a workspace.  All
+ * intermediate buffers live in one static device array of 32 MiB inside
+ * the library, reserved on every GPU that loads the library until the
+ * process exits.  Limits: 2 <= n_tips <= 512, 2 <= n_states <= 64,
+ * 1 <= n_categories <= 8, and the problem's buffers must fit in 32 MiB
+ * (e.g. 64 tips x 4,000 patterns x 4 states x 4 categories); larger
+ * problems return PHYLO_EINVAL with a message naming the bytes needed.
+ * Arguments as in phylo_set_tree / phylo_set_tip_states /
+ * phylo_set_pattern_weights / phylo_set_eigen / phylo_set_categories /
+ * phylo_set_branch_lengths (all host pointers, validated first);
+ * gradient may be NULL; error_message (may be NULL) receives up to
+ * error_capacity bytes of text on failure.
+ *
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) and sets kernel attributes for that device; make
+ * that first call before any stream capture begins.  Calls allocate no
+ * device or pinned memory.  Every call on a device shares the same array
+ * and finds it holding the previous call's contents (the call clears the
+ * one word it reads before writing).  Calls are synchronous (the stream is
+ * synchronised before returning) and serialised within a process; device
+ * work that overlaps a call while touching the same array -- e.g. a second
+ * process cannot, but kernels launched by another thread of this process
+ * from a copy of the array's address would -- races with it. */
+int phylo_evaluate_noalloc(int n_tips, int n_patterns, int n_states,
+                           int n_categories, const int32_t* parent,
+                           const uint8_t* tip_states,
+                           const double* pattern_weights, const double* V,
+                           const double* Vinv, const double* lambda,
+                           const double* root_freqs, const double* rates,
+                           const double* category_weights,
+                           const double* branch_lengths,
+                           double* log_likelihood, double* gradient,
+                           void* stream, char* error_message,
+                           size_t error_capacity);
+
 /* Release the host-side state and any CUDA objects (graph, streams) of the
  * context.  The caller frees the workspace afterwards. */
 int phylo_destroy(phylo_ctx* ctx);

@@ -54,6 +54,10 @@ SIGNATURES = {
                                     ctypes.POINTER(_c_int)]),
     "phylo_last_error": (ctypes.c_char_p, [_vp]),
     "phylo_destroy": (_c_int, [_vp]),
+    "phylo_evaluate_noalloc": (_c_int, [_c_int, _c_int, _c_int, _c_int, _ip,
+                                        _u8p, _dp, _dp, _dp, _dp, _dp, _dp,
+                                        _dp, _dp, _dp, _dp, _vp,
+                                        ctypes.c_char_p, _c_size]),
 }
 
 _lib = None

@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libphylograd.so")
 
-SOURCES = ["phylo_api.cu", "kernels_fp32.cu", "kernels_fp64.cu"]
+SOURCES = ["phylo_api.cu", "kernels_fp32.cu", "kernels_fp64.cu",
+           "phylo_noalloc.cu"]
 HEADERS = ["phylo_internal.h", "kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
