@@ -284,7 +284,12 @@ def run_ours(args):
 
     make, default_prec = _workloads()[args.workload]
     precision = args.precision or default_prec
-    w = make(rank)  # independent replica per rank
+    kw = {}
+    if args.taxa:
+        kw["n_tips"] = args.taxa
+    if args.patterns:
+        kw["n_patterns"] = args.patterns
+    w = make(rank, **kw)  # independent replica per rank
     stream = torch.cuda.current_stream()
     ctx = pg.from_workload(w, precision, stream=stream)
     K, W = args.steps, args.warmup
@@ -308,6 +313,13 @@ def run_ours(args):
     for i in range(W):
         step(i)
     ctx.check()
+    if args.profile:
+        # profiler target: the warm-up above, then K evaluations, nothing else
+        for i in range(K):
+            step(W + i)
+        ctx.check()
+        torch.cuda.synchronize()
+        return
     sampler.start()
     time.sleep(0.2)
     # -- headline: device-resident inputs, one graph per evaluation --------
@@ -473,6 +485,12 @@ def main():
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--taxa", type=int, default=None,
+                    help="override the workload's number of tips")
+    ap.add_argument("--patterns", type=int, default=None,
+                    help="override the workload's number of patterns")
+    ap.add_argument("--profile", action="store_true",
+                    help="run warm-up + K evaluations only (profiler target)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

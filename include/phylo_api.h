@@ -47,7 +47,8 @@ enum phylo_status {
   PHYLO_ENOMEM = -2,   /* workspace too small or host allocation failed    */
   PHYLO_ECUDA = -3,    /* a CUDA runtime call failed (message has details) */
   PHYLO_ESTATE = -4,   /* a required input has not been set yet            */
-  PHYLO_ENUMERIC = -5  /* the device flagged a zero/NaN partial or a bad t */
+  PHYLO_ENUMERIC = -5, /* the device flagged a zero/NaN partial or a bad t */
+  PHYLO_ETIMEOUT = -6  /* a bounded device-side wait expired (results void) */
 };
 
 enum phylo_precision {

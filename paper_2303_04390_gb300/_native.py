@@ -18,6 +18,7 @@ PHYLO_ENOMEM = -2
 PHYLO_ECUDA = -3
 PHYLO_ESTATE = -4
 PHYLO_ENUMERIC = -5
+PHYLO_ETIMEOUT = -6
 PHYLO_FP64 = 0
 PHYLO_FP32 = 1
 PHYLO_FLAG_TIP_PARTIALS = 1

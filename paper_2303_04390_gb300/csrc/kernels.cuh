@@ -22,8 +22,10 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 
 #include "phylo_internal.h"
+#include "tma.cuh"
 
 namespace phylo {
 
@@ -182,10 +184,9 @@ template <> struct Acc<double> {
 template <> struct Acc<float> {
   using type = F2;
   __device__ static F2 zero() { return {0.f, 0.f}; }
-  __device__ static F2 prod(double w, float g) {
-    const float wf = (float)w;
-    const float p = wf * g;
-    return {p, fmaf(wf, g, -p)};
+  __device__ static F2 prod(float w, float g) {
+    const float p = w * g;
+    return {p, fmaf(w, g, -p)};
   }
   __device__ static F2 add(F2 a, F2 b) { return f2_add(a, b); }
   __device__ static F2 shfl_down(F2 a, int o) {
@@ -294,32 +295,61 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Register kernels (SP <= 20): one thread per (pattern, category); the RP
-// lanes of a pattern are adjacent so the shared rescale is a shuffle.
+// Register kernels (SP <= 20): one thread per (pattern, category) for NPT
+// nodes of the level; the RP lanes of a pattern are adjacent so the shared
+// rescale is a shuffle.  Every input of the block's NPT nodes is requested
+// before any is used (more bytes in flight per warp), and the NPT x 2
+// children's matrix blocks are staged in shared memory by 1-D bulk copies
+// (cp.async.bulk) that complete on one mbarrier.
 // ---------------------------------------------------------------------------
 
-// u = P_b v_b for child b of the current node (a tip's compact state picks a
-// column of P; the gap code gives the all-ones vector).  With dM != nullptr
-// also w = dP_b v_b.  Adds the child's cumulative exponent to e.
-template <typename T, int SP, bool WITH_D>
-__device__ __forceinline__ void child_up(const LevelArgs<T>& a, int b, int c,
-                                         int r, bool active,
-                                         const T* __restrict__ M,
-                                         const T* __restrict__ dM,
-                                         T (&u)[SP], T (&w)[SP], int& e) {
+// One child's inputs for this thread's (pattern, category), loaded ahead.
+template <typename T, int SP>
+struct ChildIn {
+  T v[SP];  // partial vector (internal child or tip with partials)
+  int y;    // compact tip state, or -1
+  int e;    // the child's cumulative exponent (internal child)
+};
+
+template <typename T, int SP>
+__device__ __forceinline__ void load_child(const LevelArgs<T>& a, int b,
+                                           bool compact, int c, int r,
+                                           bool active, bool want_e,
+                                           ChildIn<T, SP>& in) {
   const int C = a.n_patterns;
-  if (b < a.n_tips && !(a.tip_has_partials && a.tip_has_partials[b])) {
-    const int y = active ? (int)a.tip_states[(size_t)b * C + c] : 0;
-    if (y < a.n_states) {
+  in.e = 0;
+  if (compact) {
+    in.y = active ? (int)a.tip_states[(size_t)b * a.state_stride + c] : 0;
+    return;
+  }
+  in.y = -1;
+  if (b < a.n_tips) {
+    load_vec<T, SP>(a.tip_partials + ((size_t)b * C + c) * SP, in.v, active);
+  } else {
+    const size_t slot = (size_t)(b - a.n_tips);
+    load_vec<T, SP>(a.post + ((slot * C + c) * a.n_cat + r) * SP, in.v, active);
+    if (want_e && active) in.e = a.escale[slot * a.escale_stride + c];
+  }
+}
+
+// u = M v (a compact state picks column y of M; the gap code gives the
+// all-ones vector), and with WITH_D also w = dM v (0 for a gap).
+template <typename T, int SP, bool WITH_D>
+__device__ __forceinline__ void child_apply(const ChildIn<T, SP>& in, int S,
+                                            const T* __restrict__ M,
+                                            const T* __restrict__ dM,
+                                            T (&u)[SP], T (&w)[SP]) {
+  if (in.y >= 0) {
+    if (in.y < S) {
 #pragma unroll
-      for (int s = 0; s < SP; ++s) u[s] = M[s * SP + y];
+      for (int s = 0; s < SP; ++s) u[s] = M[s * SP + in.y];
       if constexpr (WITH_D) {
 #pragma unroll
-        for (int s = 0; s < SP; ++s) w[s] = dM[s * SP + y];
+        for (int s = 0; s < SP; ++s) w[s] = dM[s * SP + in.y];
       }
     } else {
 #pragma unroll
-      for (int s = 0; s < SP; ++s) u[s] = s < a.n_states ? T(1) : T(0);
+      for (int s = 0; s < SP; ++s) u[s] = s < S ? T(1) : T(0);
       if constexpr (WITH_D) {
 #pragma unroll
         for (int s = 0; s < SP; ++s) w[s] = T(0);
@@ -327,186 +357,233 @@ __device__ __forceinline__ void child_up(const LevelArgs<T>& a, int b, int c,
     }
     return;
   }
-  T v[SP];
-  if (b < a.n_tips) {
-    load_vec<T, SP>(a.tip_partials + ((size_t)b * C + c) * SP, v, active);
-  } else {
-    const size_t slot = (size_t)(b - a.n_tips);
-    load_vec<T, SP>(a.post + ((slot * C + c) * a.n_cat + r) * SP, v, active);
-    if (active) e += a.escale[slot * C + c];
-  }
-  matvec<T, SP>(M, v, u);
-  if constexpr (WITH_D) matvec<T, SP>(dM, v, w);
+  matvec<T, SP>(M, in.v, u);
+  if constexpr (WITH_D) matvec<T, SP>(dM, in.v, w);
 }
 
+// Thread 0: copy the matrix blocks [b][r][SP][SP] of the listed branches
+// into shared slots [slot][r] of stride MS (16-byte aligned), one bulk copy
+// per (branch, category), all completing on `bar`.
 template <typename T, int SP, int RP>
-__device__ __forceinline__ void stage_mats(const T* __restrict__ src_base,
-                                           int b, int R, T* dst) {
+__device__ __forceinline__ void issue_mats(const T* __restrict__ base,
+                                           const int* branches, int n_br,
+                                           int R, T* dst, uint64_t* bar) {
   constexpr int MS = MatStride<T, SP>::v;
-  const T* src = src_base + (size_t)b * R * SP * SP;
-  for (int idx = threadIdx.x; idx < R * SP * SP; idx += blockDim.x) {
-    const int rr = idx / (SP * SP), e = idx % (SP * SP);
-    dst[rr * MS + e] = src[idx];
-  }
+  constexpr uint32_t bytes = SP * SP * sizeof(T);
+  for (int i = 0; i < n_br; ++i)
+    for (int q = 0; q < R; ++q)
+      bulk_g2s(dst + ((size_t)i * RP + q) * MS,
+               base + ((size_t)branches[i] * R + q) * SP * SP, bytes, bar);
 }
+
+constexpr int kDescCompactX = kDescFlagCompact0, kDescCompactY = kDescFlagCompact1;
 
 // Post-order level (Eq. 2): p_k = (P_i p_i) o (P_j p_j), rescaled; at the
 // root also log P(Y_c) (Eq. 3) weighted by W_c and summed per tile.
-template <typename T, int SP, int RP>
+template <typename T, int SP, int RP, int NPT>
 __global__ void __launch_bounds__(kSmallThreads)
 post_small_kernel(LevelArgs<T> a) {
   constexpr int NT = kSmallThreads, CT = NT / RP;
   constexpr int MS = MatStride<T, SP>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* smP[2];
-  smP[0] = reinterpret_cast<T*>(smraw);
-  smP[1] = smP[0] + RP * MS;
+  T* mats = reinterpret_cast<T*>(smraw);  // [NPT][2][RP][MS]
+  __shared__ uint64_t bar;
   __shared__ double red[NT / 32][2];
-  const int k = a.level_nodes[blockIdx.y];
-  const int2 ch = a.children[k];
+  const int g0 = blockIdx.y * NPT;
+  const int nn = min(NPT, a.n_level - g0);
   const int R = a.n_cat, C = a.n_patterns;
   const int c = blockIdx.x * CT + threadIdx.x / RP;
   const int r = threadIdx.x % RP;
   const bool valid_c = c < C;
   const bool active = valid_c && r < R;
-  stage_mats<T, SP, RP>(a.P, ch.x, R, smP[0]);
-  stage_mats<T, SP, RP>(a.P, ch.y, R, smP[1]);
-  __syncthreads();
   const int rr = r < R ? r : 0;
-  T ui[SP], uj[SP], dummy[SP];
-  int e = 0;
-  child_up<T, SP, false>(a, ch.x, c, r, active, smP[0] + rr * MS, nullptr, ui,
-                         dummy, e);
-  child_up<T, SP, false>(a, ch.y, c, r, active, smP[1] + rr * MS, nullptr, uj,
-                         dummy, e);
+  if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
+  __syncthreads();
+  int4 d[NPT];
 #pragma unroll
-  for (int s = 0; s < SP; ++s) ui[s] *= uj[s];
-  const T m = pattern_max<T, SP, RP>(ui, active);
-  e += rescale<T, SP>(ui, m, valid_c, a.err);
-  if (k != a.root) {
-    const size_t slot = (size_t)(k - a.n_tips);
-    if (active) {
-      store_vec<T, SP>(a.post + ((slot * C + c) * R + r) * SP, ui);
-      if (r == 0) a.escale[slot * C + c] = e;
+  for (int u = 0; u < NPT; ++u)
+    d[u] = u < nn ? a.level_desc[g0 + u] : make_int4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    int br[2 * NPT];
+    for (int u = 0; u < nn; ++u) { br[2 * u] = d[u].y; br[2 * u + 1] = d[u].z; }
+    mbar_expect_tx(&bar, (uint32_t)(2 * nn * R * SP * SP * sizeof(T)));
+    issue_mats<T, SP, RP>(a.P, br, 2 * nn, R, mats, &bar);
+  }
+  ChildIn<T, SP> in[NPT][2];
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    if (u < nn) {
+      load_child<T, SP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, true, in[u][0]);
+      load_child<T, SP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, true, in[u][1]);
     }
+  }
+  if (!__syncthreads_and(mbar_wait(&bar, 0))) {
+    if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
     return;
   }
-  // Root: L_c = sum_r w_r pi' p_root (Eq. 3), with the exponents restored.
-  double lr = 0.0;
-  if (active) {
 #pragma unroll
-    for (int s = 0; s < SP; ++s)
-      if (s < a.n_states) lr += a.root_pi[s] * (double)ui[s];
-    lr *= a.cat_w[r];
+  for (int u = 0; u < NPT; ++u) {
+    if (u >= nn) break;
+    const int k = d[u].x;
+    T ui[SP], uj[SP], dummy[SP];
+    child_apply<T, SP, false>(in[u][0], a.n_states, mats + ((2 * u) * RP + rr) * MS,
+                              nullptr, ui, dummy);
+    child_apply<T, SP, false>(in[u][1], a.n_states, mats + ((2 * u + 1) * RP + rr) * MS,
+                              nullptr, uj, dummy);
+#pragma unroll
+    for (int s = 0; s < SP; ++s) ui[s] *= uj[s];
+    const T m = pattern_max<T, SP, RP>(ui, active);
+    const int e = rescale<T, SP>(ui, m, valid_c, a.err) + in[u][0].e + in[u][1].e;
+    if (k != a.root) {
+      const size_t slot = (size_t)(k - a.n_tips);
+      if (active) {
+        store_vec<T, SP>(a.post + ((slot * C + c) * R + r) * SP, ui);
+        if (r == 0) a.escale[slot * a.escale_stride + c] = e;
+      }
+      continue;
+    }
+    // Root: L_c = sum_r w_r pi' p_root (Eq. 3), with the exponents restored.
+    double lr = 0.0;
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < SP; ++s)
+        if (s < a.n_states) lr += a.root_pi[s] * (double)ui[s];
+      lr *= a.cat_w[r];
+    }
+    lr = sum_over_lanes<RP>(lr);
+    double term = 0.0, unused = 0.0;
+    if (valid_c && r == 0) {
+      if (!(lr > 0.0) || !isfinite(lr)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      term = a.pattern_w[c] * (log(lr) + (double)e * 0.69314718055994530942);
+    }
+    block_sum2<NT>(term, unused, red);
+    if (threadIdx.x == 0) a.lpart[blockIdx.x] = term;
   }
-  lr = sum_over_lanes<RP>(lr);
-  double term = 0.0, unused = 0.0;
-  if (valid_c && r == 0) {
-    if (!(lr > 0.0) || !isfinite(lr)) atomicOr(a.err, ERR_ZERO_PARTIAL);
-    term = a.pattern_w[c] * (log(lr) + (double)e * 0.69314718055994530942);
-  }
-  block_sum2<NT>(term, unused, red);
-  if (threadIdx.x == 0) a.lpart[blockIdx.x] = term;
 }
 
 // Pre-order level (Eq. 4) with the fused gradient (Eq. 8): for parent k,
 //   q_i = P_i' (q_k o P_j p_j),  q_j = P_j' (q_k o P_i p_i)
 // stored (rescaled) for internal children; the ratio for branches i and j
 // is reduced over the tile's patterns with weights W_c (Eq. 7).
-template <typename T, int SP, int RP>
+template <typename T, int SP, int RP, int NPT>
 __global__ void __launch_bounds__(kSmallThreads)
 pre_small_kernel(LevelArgs<T> a) {
   constexpr int NT = kSmallThreads, CT = NT / RP;
   constexpr int MS = MatStride<T, SP>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* smP[2];
-  T* smD[2];
-  smP[0] = reinterpret_cast<T*>(smraw);
-  smP[1] = smP[0] + RP * MS;
-  smD[0] = smP[1] + RP * MS;
-  smD[1] = smD[0] + RP * MS;
+  T* mats = reinterpret_cast<T*>(smraw);  // [NPT][P_i, P_j, dP_i, dP_j][RP][MS]
+  __shared__ uint64_t bar;
   __shared__ typename Acc<T>::type red[NT / 32][2];
-  const int k = a.level_nodes[blockIdx.y];
-  const int2 ch = a.children[k];
+  const int g0 = blockIdx.y * NPT;
+  const int nn = min(NPT, a.n_level - g0);
   const int R = a.n_cat, C = a.n_patterns;
   const int c = blockIdx.x * CT + threadIdx.x / RP;
   const int r = threadIdx.x % RP;
   const bool valid_c = c < C;
   const bool active = valid_c && r < R;
-  stage_mats<T, SP, RP>(a.P, ch.x, R, smP[0]);
-  stage_mats<T, SP, RP>(a.P, ch.y, R, smP[1]);
-  stage_mats<T, SP, RP>(a.dP, ch.x, R, smD[0]);
-  stage_mats<T, SP, RP>(a.dP, ch.y, R, smD[1]);
-  __syncthreads();
   const int rr = r < R ? r : 0;
-  T q[SP];
-  if (k == a.root) {
+  if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
+  __syncthreads();
+  int4 d[NPT];
 #pragma unroll
-    for (int s = 0; s < SP; ++s)
-      q[s] = (active && s < a.n_states) ? (T)a.root_pi[s] : T(0);
-  } else {
-    const size_t slot = (size_t)(k - a.n_tips);
-    load_vec<T, SP>(a.pre + ((slot * C + c) * R + r) * SP, q, active);
-  }
-  T ui[SP], vi[SP], uj[SP], vj[SP];
-  int e_unused = 0;
-  child_up<T, SP, true>(a, ch.x, c, r, active, smP[0] + rr * MS,
-                        smD[0] + rr * MS, ui, vi, e_unused);
-  child_up<T, SP, true>(a, ch.y, c, r, active, smP[1] + rr * MS,
-                        smD[1] + rr * MS, uj, vj, e_unused);
-  // Per-category numerators and the shared denominator.
-  T num_i = T(0), num_j = T(0), den = T(0);
-#pragma unroll
-  for (int s = 0; s < SP; ++s) {
-    const T qi = q[s] * uj[s];  // a_i
-    const T qj = q[s] * ui[s];  // a_j
-    num_i = fma(qi, vi[s], num_i);
-    num_j = fma(qj, vj[s], num_j);
-    den = fma(qi, ui[s], den);
-  }
-  // sum over categories (Eq. 8) in T, then the ratio in T
-  const T w = active ? (T)a.cat_w[r] : T(0);
-  const T Ni = sum_over_lanes<RP>(w * num_i);
-  const T Nj = sum_over_lanes<RP>(w * num_j);
-  const T D = sum_over_lanes<RP>(w * den);
-  using A = Acc<T>;
-  typename A::type gi = A::zero(), gj = A::zero();
-  if (valid_c && r == 0) {
-    if (!(D > T(0)) || !isfinite(D)) {
-      atomicOr(a.err, ERR_BAD_RATIO);
-    } else {
-      const double W = a.pattern_w[c];
-      gi = A::prod(W, Ni / D);
-      gj = A::prod(W, Nj / D);
+  for (int u = 0; u < NPT; ++u)
+    d[u] = u < nn ? a.level_desc[g0 + u] : make_int4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    int br[2 * NPT];
+    mbar_expect_tx(&bar, (uint32_t)(4 * nn * R * SP * SP * sizeof(T)));
+    for (int u = 0; u < nn; ++u) {
+      br[0] = d[u].y;
+      br[1] = d[u].z;
+      issue_mats<T, SP, RP>(a.P, br, 2, R, mats + (size_t)(4 * u) * RP * MS, &bar);
+      issue_mats<T, SP, RP>(a.dP, br, 2, R, mats + (size_t)(4 * u + 2) * RP * MS, &bar);
     }
   }
-  // Children's pre-order partials (internal children only).
-  if (ch.x >= a.n_tips) {
-    T av[SP], out[SP];
+  T q[NPT][SP];
+  ChildIn<T, SP> in[NPT][2];
 #pragma unroll
-    for (int s = 0; s < SP; ++s) av[s] = q[s] * uj[s];
-    matvec_t<T, SP>(smP[0] + rr * MS, av, out);
-    const T m = pattern_max<T, SP, RP>(out, active);
-    rescale<T, SP>(out, m, valid_c, a.err);
-    if (active)
-      store_vec<T, SP>(
-          a.pre + (((size_t)(ch.x - a.n_tips) * C + c) * R + r) * SP, out);
-  }
-  if (ch.y >= a.n_tips) {
-    T av[SP], out[SP];
+  for (int u = 0; u < NPT; ++u) {
+    if (u < nn) {
+      const int k = d[u].x;
+      if (k == a.root) {
 #pragma unroll
-    for (int s = 0; s < SP; ++s) av[s] = q[s] * ui[s];
-    matvec_t<T, SP>(smP[1] + rr * MS, av, out);
-    const T m = pattern_max<T, SP, RP>(out, active);
-    rescale<T, SP>(out, m, valid_c, a.err);
-    if (active)
-      store_vec<T, SP>(
-          a.pre + (((size_t)(ch.y - a.n_tips) * C + c) * R + r) * SP, out);
+        for (int s = 0; s < SP; ++s)
+          q[u][s] = (active && s < a.n_states) ? (T)a.root_pi[s] : T(0);
+      } else {
+        load_vec<T, SP>(a.pre + (((size_t)(k - a.n_tips) * C + c) * R + r) * SP, q[u],
+                        active);
+      }
+      load_child<T, SP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, false, in[u][0]);
+      load_child<T, SP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, false, in[u][1]);
+    }
   }
-  block_sum_acc<T, NT>(gi, gj, red, RP);
-  if (threadIdx.x == 0) {
-    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = A::to_double(gi);
-    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = A::to_double(gj);
+  if (!__syncthreads_and(mbar_wait(&bar, 0))) {
+    if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
+    return;
+  }
+  using A = Acc<T>;
+  const T w = active ? a.cat_wt[r] : T(0);
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    if (u >= nn) break;
+    const int bi = d[u].y, bj = d[u].z;
+    const T* Pi = mats + ((4 * u) * RP + rr) * MS;
+    const T* Pj = mats + ((4 * u + 1) * RP + rr) * MS;
+    const T* Di = mats + ((4 * u + 2) * RP + rr) * MS;
+    const T* Dj = mats + ((4 * u + 3) * RP + rr) * MS;
+    T ui[SP], vi[SP], uj[SP], vj[SP];
+    child_apply<T, SP, true>(in[u][0], a.n_states, Pi, Di, ui, vi);
+    child_apply<T, SP, true>(in[u][1], a.n_states, Pj, Dj, uj, vj);
+    // Per-category numerators and the shared denominator.
+    T num_i = T(0), num_j = T(0), den = T(0);
+#pragma unroll
+    for (int s = 0; s < SP; ++s) {
+      const T qi = q[u][s] * uj[s];  // a_i
+      const T qj = q[u][s] * ui[s];  // a_j
+      num_i = fma(qi, vi[s], num_i);
+      num_j = fma(qj, vj[s], num_j);
+      den = fma(qi, ui[s], den);
+    }
+    // sum over categories (Eq. 8) in T, then the ratio in T
+    const T Ni = sum_over_lanes<RP>(w * num_i);
+    const T Nj = sum_over_lanes<RP>(w * num_j);
+    const T D = sum_over_lanes<RP>(w * den);
+    typename A::type gi = A::zero(), gj = A::zero();
+    if (valid_c && r == 0) {
+      if (!(D > T(0)) || !isfinite(D)) {
+        atomicOr(a.err, ERR_BAD_RATIO);
+      } else {
+        const T W = a.pattern_wt[c];
+        gi = A::prod(W, Ni / D);
+        gj = A::prod(W, Nj / D);
+      }
+    }
+    // Children's pre-order partials (internal children only).
+    if (bi >= a.n_tips) {
+      T av[SP], out[SP];
+#pragma unroll
+      for (int s = 0; s < SP; ++s) av[s] = q[u][s] * uj[s];
+      matvec_t<T, SP>(Pi, av, out);
+      const T m = pattern_max<T, SP, RP>(out, active);
+      rescale<T, SP>(out, m, valid_c, a.err);
+      if (active)
+        store_vec<T, SP>(a.pre + (((size_t)(bi - a.n_tips) * C + c) * R + r) * SP, out);
+    }
+    if (bj >= a.n_tips) {
+      T av[SP], out[SP];
+#pragma unroll
+      for (int s = 0; s < SP; ++s) av[s] = q[u][s] * ui[s];
+      matvec_t<T, SP>(Pj, av, out);
+      const T m = pattern_max<T, SP, RP>(out, active);
+      rescale<T, SP>(out, m, valid_c, a.err);
+      if (active)
+        store_vec<T, SP>(a.pre + (((size_t)(bj - a.n_tips) * C + c) * R + r) * SP, out);
+    }
+    block_sum_acc<T, NT>(gi, gj, red, RP);
+    if (threadIdx.x == 0) {
+      a.gpart[(size_t)bi * a.n_tiles + blockIdx.x] = A::to_double(gi);
+      a.gpart[(size_t)bj * a.n_tiles + blockIdx.x] = A::to_double(gj);
+    }
+    __syncthreads();  // red[] is reused by the next node
   }
 }
 
@@ -545,7 +622,7 @@ __device__ __forceinline__ void stage_child_vec(const LevelArgs<T>& a, int b,
   if (compact) {
     for (int j = threadIdx.x; j < CT; j += blockDim.x) {
       const int c = c0 + j;
-      ystate[j] = c < C ? (int)a.tip_states[(size_t)b * C + c] : 0;
+      ystate[j] = c < C ? (int)a.tip_states[(size_t)b * a.state_stride + c] : 0;
     }
     return;
   }
@@ -636,8 +713,8 @@ __global__ void __launch_bounds__(kWideThreads) post_wide_kernel(LevelArgs<T> a)
     const int j = g * CPG + jj, c = c0 + j;
     int e = 0;
     if (c < C) {
-      if (ch.x >= a.n_tips) e += a.escale[(size_t)(ch.x - a.n_tips) * C + c];
-      if (ch.y >= a.n_tips) e += a.escale[(size_t)(ch.y - a.n_tips) * C + c];
+      if (ch.x >= a.n_tips) e += a.escale[(size_t)(ch.x - a.n_tips) * a.escale_stride + c];
+      if (ch.y >= a.n_tips) e += a.escale[(size_t)(ch.y - a.n_tips) * a.escale_stride + c];
     }
     eacc[jj] = e;
   }
@@ -671,7 +748,7 @@ __global__ void __launch_bounds__(kWideThreads) post_wide_kernel(LevelArgs<T> a)
         for (int r = 0; r < R; ++r)
           a.post[((slot * C + c) * R + r) * kWideSP + s] =
               sm.pk[r][j * kWideSP + s] * f;
-        if (s == 0) a.escale[slot * C + c] = etot;
+        if (s == 0) a.escale[slot * a.escale_stride + c] = etot;
       }
     } else {
       // root: sum_r w_r pi' p over the group's 64 threads
@@ -749,7 +826,7 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
       sm.qk[idx] = v;
     }
     __syncthreads();
-    const T wr = (T)a.cat_w[r];
+    const T wr = a.cat_wt[r];
 #pragma unroll
     for (int jj = 0; jj < CPG; ++jj) {
       const int j = g * CPG + jj;
@@ -828,8 +905,8 @@ __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) 
       if (!(D > T(0)) || !isfinite(D)) {
         atomicOr(a.err, ERR_BAD_RATIO);
       } else {
-        gi = A::add(gi, A::prod(a.pattern_w[c], Ni / D));
-        gj = A::add(gj, A::prod(a.pattern_w[c], Nj / D));
+        gi = A::add(gi, A::prod(a.pattern_wt[c], Ni / D));
+        gj = A::add(gj, A::prod(a.pattern_wt[c], Nj / D));
       }
     }
     for (int x = 0; x < 2; ++x) {
@@ -862,35 +939,53 @@ inline size_t wide_pre_smem(int R) {
          (size_t)2 * R * WideCfg<T>::CT * kWideSP * sizeof(T);
 }
 
+}  // namespace phylo
+
+#include "kernels_p4.cuh"
+
+namespace phylo {
+
 // ---------------------------------------------------------------------------
 // Instantiation of the launchers for one element type.
 // ---------------------------------------------------------------------------
-template <typename T, int SP, int RP>
+// Nodes per block of the register kernels: more inputs in flight per warp,
+// bounded by registers (the inputs of all NPT nodes are held at once).
+template <typename T, int SP>
+struct SmallNpt {
+  static constexpr int post = (SP == 4) ? 4 : 2;
+  static constexpr int pre = (SP == 4) ? (sizeof(T) == 4 ? 4 : 2) : 1;
+};
+
+template <typename T, int SP, int RP, int NPT>
 constexpr size_t small_smem(bool post) {
-  return (size_t)(post ? 2 : 4) * RP * MatStride<T, SP>::v * sizeof(T);
+  return (size_t)NPT * (post ? 2 : 4) * RP * MatStride<T, SP>::v * sizeof(T);
 }
 
 template <typename T, int SP, int RP>
 cudaError_t launch_small(const LevelArgs<T>& a, bool post, cudaStream_t st) {
-  dim3 grid(a.n_tiles, a.n_level);
-  if (post)
-    post_small_kernel<T, SP, RP>
-        <<<grid, kSmallThreads, small_smem<T, SP, RP>(true), st>>>(a);
-  else
-    pre_small_kernel<T, SP, RP>
-        <<<grid, kSmallThreads, small_smem<T, SP, RP>(false), st>>>(a);
+  constexpr int NPo = SmallNpt<T, SP>::post, NPr = SmallNpt<T, SP>::pre;
+  if (post) {
+    dim3 grid(a.n_tiles, (a.n_level + NPo - 1) / NPo);
+    post_small_kernel<T, SP, RP, NPo>
+        <<<grid, kSmallThreads, small_smem<T, SP, RP, NPo>(true), st>>>(a);
+  } else {
+    dim3 grid(a.n_tiles, (a.n_level + NPr - 1) / NPr);
+    pre_small_kernel<T, SP, RP, NPr>
+        <<<grid, kSmallThreads, small_smem<T, SP, RP, NPr>(false), st>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <typename T, int SP, int RP>
 cudaError_t prepare_small() {
+  constexpr int NPo = SmallNpt<T, SP>::post, NPr = SmallNpt<T, SP>::pre;
   cudaError_t e = cudaFuncSetAttribute(
-      post_small_kernel<T, SP, RP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)small_smem<T, SP, RP>(true));
+      post_small_kernel<T, SP, RP, NPo>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)small_smem<T, SP, RP, NPo>(true));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(pre_small_kernel<T, SP, RP>,
+  return cudaFuncSetAttribute(pre_small_kernel<T, SP, RP, NPr>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)small_smem<T, SP, RP>(false));
+                              (int)small_smem<T, SP, RP, NPr>(false));
 }
 
 template <typename T, int SP>
@@ -921,7 +1016,9 @@ cudaError_t launch_level_impl(const LevelArgs<T>& a, int SP, int RP, bool post,
                               cudaStream_t st) {
   if (a.n_tiles <= 0 || a.n_level <= 0) return cudaSuccess;
   switch (SP) {
-    case 4: return launch_small_rp<T, 4>(a, RP, post, st);
+    case 4:
+      if constexpr (std::is_same<T, float>::value) return launch_p4_rp(a, RP, post, st);
+      else return launch_small_rp<T, 4>(a, RP, post, st);
     case 20: return launch_small_rp<T, 20>(a, RP, post, st);
     case 64: {
       dim3 grid(a.n_tiles, a.n_level);

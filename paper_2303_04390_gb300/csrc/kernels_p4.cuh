@@ -1,0 +1,338 @@
+// FP32 level kernels for 4 padded states (nucleotide models): one thread
+// per pattern, covering every rate category.
+//
+// Arithmetic as in the register kernels of kernels.cuh (Eq. 2 with the
+// root's Eq. 3; Eq. 4 with the fused Eq. 8 ratio and Eq. 7 tile sums).  The
+// mapping is chosen for S = 4, where a (pattern, category) pair carries too
+// little work to pay for per-pair shuffles:
+//  - a thread owns one pattern and all R <= RM categories, so the rescale
+//    maximum, the sums over categories and the gradient ratio are local;
+//  - the thread issues every 16-byte load of its pattern (R vectors per
+//    input) before it computes, so each warp keeps 3 x R x 512 bytes in
+//    flight;
+//  - the block's transition matrices are staged in shared memory by 1-D
+//    bulk copies (cp.async.bulk) on an mbarrier, then transposed once per
+//    block so that P v, dP v and P' a all run on the packed FP32 FMA
+//    (__ffma2_rn, two lanes per instruction) from 16-byte broadcast reads;
+//  - the tile's gradient sums are FP32 pairs kept exact with error-free
+//    transformations (converted to FP64 once per tile).
+#pragma once
+
+namespace phylo {
+
+constexpr int kP4Threads = kP4TilePatterns;  // patterns per block (one tile)
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+// out = M v for 4x4 M given by the rows of M' (t-th row = column t of M).
+__device__ __forceinline__ void mv4t(const float4* __restrict__ MT, float4 v,
+                                     float2& lo, float2& hi) {
+  const float4 c0 = MT[0], c1 = MT[1], c2 = MT[2], c3 = MT[3];
+  lo = __fmul2_rn(lo2(c0), make_float2(v.x, v.x));
+  hi = __fmul2_rn(hi2(c0), make_float2(v.x, v.x));
+  lo = __ffma2_rn(lo2(c1), make_float2(v.y, v.y), lo);
+  hi = __ffma2_rn(hi2(c1), make_float2(v.y, v.y), hi);
+  lo = __ffma2_rn(lo2(c2), make_float2(v.z, v.z), lo);
+  hi = __ffma2_rn(hi2(c2), make_float2(v.z, v.z), hi);
+  lo = __ffma2_rn(lo2(c3), make_float2(v.w, v.w), lo);
+  hi = __ffma2_rn(hi2(c3), make_float2(v.w, v.w), hi);
+}
+
+// out = M' a for 4x4 M given by its rows.
+__device__ __forceinline__ void mtv4r(const float4* __restrict__ M, float2 alo,
+                                      float2 ahi, float2& lo, float2& hi) {
+  const float4 r0 = M[0], r1 = M[1], r2 = M[2], r3 = M[3];
+  lo = __fmul2_rn(lo2(r0), make_float2(alo.x, alo.x));
+  hi = __fmul2_rn(hi2(r0), make_float2(alo.x, alo.x));
+  lo = __ffma2_rn(lo2(r1), make_float2(alo.y, alo.y), lo);
+  hi = __ffma2_rn(hi2(r1), make_float2(alo.y, alo.y), hi);
+  lo = __ffma2_rn(lo2(r2), make_float2(ahi.x, ahi.x), lo);
+  hi = __ffma2_rn(hi2(r2), make_float2(ahi.x, ahi.x), hi);
+  lo = __ffma2_rn(lo2(r3), make_float2(ahi.y, ahi.y), lo);
+  hi = __ffma2_rn(hi2(r3), make_float2(ahi.y, ahi.y), hi);
+}
+
+__device__ __forceinline__ float dot22(float2 alo, float2 ahi, float2 blo,
+                                       float2 bhi) {
+  float2 x = __fmul2_rn(alo, blo);
+  x = __ffma2_rn(ahi, bhi, x);
+  return x.x + x.y;
+}
+
+__device__ __forceinline__ float max4(float2 lo, float2 hi) {
+  return fmaxf(fmaxf(fabsf(lo.x), fabsf(lo.y)), fmaxf(fabsf(hi.x), fabsf(hi.y)));
+}
+
+// Shared layout of one block: for each staged matrix block m (R x 16
+// floats, category-major) a raw copy and its per-category transpose.
+template <int RM>
+struct P4Mats {
+  float4 raw[4][RM * 4];  // P_i, P_j, dP_i, dP_j as copied (rows)
+  float4 tr[4][RM * 4];   // their transposes (rows of M' = columns of M)
+};
+
+// The child's 4 states for category r: u = M v (and w = dM v), a compact
+// state selecting a column (gap: all ones, w = 0).
+template <bool WITH_D>
+__device__ __forceinline__ void p4_child(int y, int S, float4 v,
+                                         const float4* MT, const float4* DT,
+                                         float2& ulo, float2& uhi, float2& wlo,
+                                         float2& whi) {
+  if (y >= 0) {
+    if (y < S) {
+      const float4 col = MT[y];
+      ulo = lo2(col); uhi = hi2(col);
+      if (WITH_D) { const float4 dc = DT[y]; wlo = lo2(dc); whi = hi2(dc); }
+    } else {
+      ulo = make_float2(1.f, S > 1 ? 1.f : 0.f);
+      uhi = make_float2(S > 2 ? 1.f : 0.f, S > 3 ? 1.f : 0.f);
+      if (WITH_D) { wlo = make_float2(0.f, 0.f); whi = wlo; }
+    }
+    return;
+  }
+  mv4t(MT, v, ulo, uhi);
+  if (WITH_D) mv4t(DT, v, wlo, whi);
+}
+
+template <int RM, bool PRE>
+__global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a) {
+  __shared__ P4Mats<RM> sm;
+  __shared__ uint64_t bar;
+  __shared__ F2 red[kP4Threads / 32][2];
+  __shared__ double lred[kP4Threads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int4 d = a.level_desc[blockIdx.y];
+  const int k = d.x, bi = d.y, bj = d.z;
+  const bool ci = d.w & kDescFlagCompact0, cj = d.w & kDescFlagCompact1;
+  const int c = blockIdx.x * kP4Threads + tid;
+  const bool valid = c < C;
+  const uint32_t mbytes = (uint32_t)R * 64;
+  if (tid == 0) mbar_init_fenced(&bar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&bar, mbytes * (PRE ? 4 : 2));
+    bulk_g2s(sm.raw[0], a.P + (size_t)bi * R * 16, mbytes, &bar);
+    bulk_g2s(sm.raw[1], a.P + (size_t)bj * R * 16, mbytes, &bar);
+    if (PRE) {
+      bulk_g2s(sm.raw[2], a.dP + (size_t)bi * R * 16, mbytes, &bar);
+      bulk_g2s(sm.raw[3], a.dP + (size_t)bj * R * 16, mbytes, &bar);
+    }
+  }
+  // ---- every global load of this pattern, issued before any use ----------
+  float4 vi[RM], vj[RM], q[RM];
+  int yi = -1, yj = -1, ei = 0, ej = 0;
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (valid) {
+    if (ci) yi = a.tip_states[(size_t)bi * a.state_stride + c];
+    if (cj) yj = a.tip_states[(size_t)bj * a.state_stride + c];
+  }
+#pragma unroll
+  for (int r = 0; r < RM; ++r) {
+    const bool on = valid && r < R;
+    vi[r] = zero4; vj[r] = zero4; q[r] = zero4;
+    if (on && !ci)
+      vi[r] = bi < a.n_tips ? __ldg(reinterpret_cast<const float4*>(a.tip_partials) + (size_t)bi * C + c)
+                            : __ldg(reinterpret_cast<const float4*>(a.post) +
+                                    ((size_t)(bi - a.n_tips) * C + c) * R + r);
+    if (on && !cj)
+      vj[r] = bj < a.n_tips ? __ldg(reinterpret_cast<const float4*>(a.tip_partials) + (size_t)bj * C + c)
+                            : __ldg(reinterpret_cast<const float4*>(a.post) +
+                                    ((size_t)(bj - a.n_tips) * C + c) * R + r);
+    if (PRE && on && k != a.root)
+      q[r] = __ldg(reinterpret_cast<const float4*>(a.pre) +
+                   ((size_t)(k - a.n_tips) * C + c) * R + r);
+  }
+  if (!PRE && valid) {
+    if (bi >= a.n_tips) ei = a.escale[(size_t)(bi - a.n_tips) * a.escale_stride + c];
+    if (bj >= a.n_tips) ej = a.escale[(size_t)(bj - a.n_tips) * a.escale_stride + c];
+  }
+  // ---- matrices: wait for the bulk copies, transpose once per block ------
+  if (!__syncthreads_and(mbar_wait(&bar, 0))) {
+    if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
+    return;
+  }
+  {
+    const float* raw = reinterpret_cast<const float*>(sm.raw);
+    float* tr = reinterpret_cast<float*>(sm.tr);
+    const int n = (PRE ? 4 : 2) * RM * 16;
+    for (int i = tid; i < n; i += kP4Threads) {
+      const int m = i / (RM * 16), rem = i % (RM * 16), rr = rem / 16, e = rem % 16;
+      const int s = e / 4, t = e % 4;  // tr[m][rr][t][s] = raw[m][rr][s][t]
+      tr[(m * RM + rr) * 16 + t * 4 + s] = raw[(m * RM + rr) * 16 + s * 4 + t];
+    }
+  }
+  __syncthreads();
+  if (!PRE) {
+    // ---- Eq. 2: p_k = (P_i p_i) o (P_j p_j) for every category ------------
+    float2 plo[RM], phi[RM];
+    float m = 0.f;
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+      plo[r] = make_float2(0.f, 0.f); phi[r] = plo[r];
+      if (r < R) {
+        float2 ilo, ihi, jlo, jhi, d0, d1;
+        p4_child<false>(yi, S, vi[r], sm.tr[0] + r * 4, nullptr, ilo, ihi, d0, d1);
+        p4_child<false>(yj, S, vj[r], sm.tr[1] + r * 4, nullptr, jlo, jhi, d0, d1);
+        plo[r] = __fmul2_rn(ilo, jlo);
+        phi[r] = __fmul2_rn(ihi, jhi);
+        m = fmaxf(m, max4(plo[r], phi[r]));
+      }
+    }
+    int e = 0;
+    if (valid) {
+      if (!(m > 0.f) || !isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else (void)frexpf(m, &e);
+    }
+    const float f = ldexpf(1.f, -e);
+    e += ei + ej;
+    if (k != a.root) {
+      if (valid) {
+        float4* out = reinterpret_cast<float4*>(a.post) + ((size_t)(k - a.n_tips) * C + c) * R;
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+          if (r < R) {
+            const float2 lo = __fmul2_rn(plo[r], make_float2(f, f));
+            const float2 hi = __fmul2_rn(phi[r], make_float2(f, f));
+            out[r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+          }
+        a.escale[(size_t)(k - a.n_tips) * a.escale_stride + c] = e;
+      }
+      return;
+    }
+    // Eq. 3 at the root: L_c = sum_r w_r pi' p_root,r,c, exponents restored
+    double term = 0.0;
+    if (valid) {
+      const float2 pl = make_float2((float)a.root_pi[0], S > 1 ? (float)a.root_pi[1] : 0.f);
+      const float2 ph = make_float2(S > 2 ? (float)a.root_pi[2] : 0.f, S > 3 ? (float)a.root_pi[3] : 0.f);
+      float L = 0.f;
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+        if (r < R) L = fmaf(a.cat_wt[r], dot22(pl, ph, plo[r], phi[r]) * f, L);
+      if (!(L > 0.f) || !isfinite(L)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      term = (double)a.pattern_wt[c] * (log((double)L) + (double)e * 0.69314718055994530942);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(kFull, term, o);
+    if (lane == 0) lred[warp] = term;
+    __syncthreads();
+    if (tid == 0) {
+      double l = 0.0;
+      for (int w = 0; w < kP4Threads / 32; ++w) l += lred[w];
+      a.lpart[blockIdx.x] = l;
+    }
+    return;
+  }
+  // ---- Eq. 4 and Eq. 8: children's pre-order partials and the ratio ------
+  float2 rootlo = make_float2(0.f, 0.f), roothi = rootlo;
+  if (k == a.root) {
+    rootlo = make_float2((float)a.root_pi[0], S > 1 ? (float)a.root_pi[1] : 0.f);
+    roothi = make_float2(S > 2 ? (float)a.root_pi[2] : 0.f, S > 3 ? (float)a.root_pi[3] : 0.f);
+  }
+  const bool int_i = bi >= a.n_tips, int_j = bj >= a.n_tips;
+  float2 qilo[RM], qihi[RM], qjlo[RM], qjhi[RM];
+  float Ni = 0.f, Nj = 0.f, Dn = 0.f, mi = 0.f, mj = 0.f;
+#pragma unroll
+  for (int r = 0; r < RM; ++r) {
+    qilo[r] = make_float2(0.f, 0.f); qihi[r] = qilo[r]; qjlo[r] = qilo[r]; qjhi[r] = qilo[r];
+    if (r < R) {
+      const float2 ql = k == a.root ? rootlo : lo2(q[r]);
+      const float2 qh = k == a.root ? roothi : hi2(q[r]);
+      float2 uilo, uihi, wilo, wihi, ujlo, ujhi, wjlo, wjhi;
+      p4_child<true>(yi, S, vi[r], sm.tr[0] + r * 4, sm.tr[2] + r * 4, uilo, uihi, wilo, wihi);
+      p4_child<true>(yj, S, vj[r], sm.tr[1] + r * 4, sm.tr[3] + r * 4, ujlo, ujhi, wjlo, wjhi);
+      const float2 ailo = __fmul2_rn(ql, ujlo), aihi = __fmul2_rn(qh, ujhi);  // a_i
+      const float2 ajlo = __fmul2_rn(ql, uilo), ajhi = __fmul2_rn(qh, uihi);  // a_j
+      const float w = a.cat_wt[r];
+      Ni = fmaf(w, dot22(ailo, aihi, wilo, wihi), Ni);
+      Nj = fmaf(w, dot22(ajlo, ajhi, wjlo, wjhi), Nj);
+      Dn = fmaf(w, dot22(ailo, aihi, uilo, uihi), Dn);
+      if (int_i) {
+        mtv4r(sm.raw[0] + r * 4, ailo, aihi, qilo[r], qihi[r]);
+        mi = fmaxf(mi, max4(qilo[r], qihi[r]));
+      }
+      if (int_j) {
+        mtv4r(sm.raw[1] + r * 4, ajlo, ajhi, qjlo[r], qjhi[r]);
+        mj = fmaxf(mj, max4(qjlo[r], qjhi[r]));
+      }
+    }
+  }
+  F2 gi = {0.f, 0.f}, gj = {0.f, 0.f};
+  if (valid) {
+    if (!(Dn > 0.f) || !isfinite(Dn)) {
+      atomicOr(a.err, ERR_BAD_RATIO);
+    } else {
+      const float W = a.pattern_wt[c];
+      gi = Acc<float>::prod(W, Ni / Dn);
+      gj = Acc<float>::prod(W, Nj / Dn);
+    }
+    if (int_i) {
+      int e = 0;
+      if (!(mi > 0.f) || !isfinite(mi)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else (void)frexpf(mi, &e);
+      const float f = ldexpf(1.f, -e);
+      float4* out = reinterpret_cast<float4*>(a.pre) + ((size_t)(bi - a.n_tips) * C + c) * R;
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+        if (r < R) {
+          const float2 lo = __fmul2_rn(qilo[r], make_float2(f, f));
+          const float2 hi = __fmul2_rn(qihi[r], make_float2(f, f));
+          out[r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+    }
+    if (int_j) {
+      int e = 0;
+      if (!(mj > 0.f) || !isfinite(mj)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else (void)frexpf(mj, &e);
+      const float f = ldexpf(1.f, -e);
+      float4* out = reinterpret_cast<float4*>(a.pre) + ((size_t)(bj - a.n_tips) * C + c) * R;
+#pragma unroll
+      for (int r = 0; r < RM; ++r)
+        if (r < R) {
+          const float2 lo = __fmul2_rn(qjlo[r], make_float2(f, f));
+          const float2 hi = __fmul2_rn(qjhi[r], make_float2(f, f));
+          out[r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    gi = f2_add(gi, Acc<float>::shfl_down(gi, o));
+    gj = f2_add(gj, Acc<float>::shfl_down(gj, o));
+  }
+  if (lane == 0) { red[warp][0] = gi; red[warp][1] = gj; }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < kP4Threads / 32; ++w) {
+      gi = f2_add(gi, red[w][0]);
+      gj = f2_add(gj, red[w][1]);
+    }
+    a.gpart[(size_t)bi * a.n_tiles + blockIdx.x] = Acc<float>::to_double(gi);
+    a.gpart[(size_t)bj * a.n_tiles + blockIdx.x] = Acc<float>::to_double(gj);
+  }
+}
+
+template <int RM>
+cudaError_t launch_p4(const LevelArgs<float>& a, bool post, cudaStream_t st) {
+  dim3 grid(a.n_tiles, a.n_level);
+  if (post)
+    level_p4_kernel<RM, false><<<grid, kP4Threads, 0, st>>>(a);
+  else
+    level_p4_kernel<RM, true><<<grid, kP4Threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// RP (next power of two >= R) selects the unrolled category count.
+inline cudaError_t launch_p4_rp(const LevelArgs<float>& a, int RP, bool post,
+                                cudaStream_t st) {
+  switch (RP) {
+    case 1: return launch_p4<1>(a, post, st);
+    case 2: return launch_p4<2>(a, post, st);
+    case 4: return launch_p4<4>(a, post, st);
+    case 8: return launch_p4<8>(a, post, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace phylo

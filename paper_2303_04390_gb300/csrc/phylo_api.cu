@@ -35,10 +35,11 @@ struct Region {
 struct Layout {
   int SP = 0, RP = 0, n_tiles = 0;
   size_t elem = 0;
-  Region children, post_nodes, pre_nodes;
+  Region children, post_nodes, pre_nodes, post_desc, pre_desc;
   Region P, dP, post, pre, escale;
   Region tip_states, tip_partials, tip_has;
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
+  Region pattern_wt, cat_wt;  // the weights in the path's element type
   Region gpart, lpart, out;  // out = [logL, grad...] followed by the flag word
   size_t total = 0;
 };
@@ -81,14 +82,18 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.children, n_nodes * sizeof(int2));
   ok &= add_region(L, L.post_nodes, n_int * sizeof(int));
   ok &= add_region(L, L.pre_nodes, n_int * sizeof(int));
+  ok &= add_region(L, L.post_desc, n_int * sizeof(int4));
+  ok &= add_region(L, L.pre_desc, n_int * sizeof(int4));
   ok &= add_region(L, L.P, mat);
   ok &= add_region(L, L.dP, mat);
   ok &= add_region(L, L.post, part);
   ok &= add_region(L, L.pre, part);
-  if (!mul_ok(n_int, (size_t)C * sizeof(int), &tmp)) return "size overflow";
+  if (C > (1 << 30)) return "n_patterns too large";
+  if (!mul_ok(n_int, (size_t)round_up(C, 4) * sizeof(int), &tmp)) return "size overflow";
   ok &= add_region(L, L.escale, tmp);
-  if (!mul_ok((size_t)N, (size_t)C, &tmp)) return "size overflow";
+  if (!mul_ok((size_t)N, (size_t)round_up(C, 16), &tmp)) return "size overflow";
   ok &= add_region(L, L.tip_states, tmp);
+  if (!mul_ok((size_t)N, (size_t)C, &tmp)) return "size overflow";
   if (flags & PHYLO_FLAG_TIP_PARTIALS) {
     if (!mul_ok(tmp, (size_t)L.SP * L.elem, &tmp2)) return "size overflow";
     ok &= add_region(L, L.tip_partials, tmp2);
@@ -101,6 +106,8 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.pi, (size_t)S * 8);
   ok &= add_region(L, L.rates, (size_t)R * 8);
   ok &= add_region(L, L.cat_w, (size_t)R * 8);
+  ok &= add_region(L, L.pattern_wt, (size_t)C * L.elem);
+  ok &= add_region(L, L.cat_wt, (size_t)R * L.elem);
   ok &= add_region(L, L.t, n_br * 8);
   if (!mul_ok(n_br, (size_t)L.n_tiles * 8, &tmp)) return "size overflow";
   ok &= add_region(L, L.gpart, tmp);
@@ -194,6 +201,8 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.pre = ctx->dev<T>(ctx->L.pre);
   a.escale = ctx->dev<int>(ctx->L.escale);
   a.tip_states = ctx->dev<uint8_t>(ctx->L.tip_states);
+  a.state_stride = round_up(ctx->C, 16);
+  a.escale_stride = round_up(ctx->C, 4);
   bool any_partials = false;
   for (int v : ctx->tip_has) any_partials |= v != 0;
   a.tip_partials = any_partials ? ctx->dev<T>(ctx->L.tip_partials) : nullptr;
@@ -201,6 +210,8 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.pattern_w = ctx->dev<double>(ctx->L.pattern_w);
   a.root_pi = ctx->dev<double>(ctx->L.pi);
   a.cat_w = ctx->dev<double>(ctx->L.cat_w);
+  a.pattern_wt = ctx->dev<T>(ctx->L.pattern_wt);
+  a.cat_wt = ctx->dev<T>(ctx->L.cat_wt);
   a.gpart = ctx->dev<double>(ctx->L.gpart);
   a.lpart = ctx->dev<double>(ctx->L.lpart);
   a.n_tiles = ctx->L.n_tiles;
@@ -241,9 +252,11 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     LevelArgs<T> a = level_args<T>(ctx);
     const bool post = phase == 1;
     const int* nodes = ctx->dev<int>(post ? ctx->L.post_nodes : ctx->L.pre_nodes);
+    const int4* desc = ctx->dev<int4>(post ? ctx->L.post_desc : ctx->L.pre_desc);
     const std::vector<int>& off = post ? ctx->post_off : ctx->pre_off;
     for (size_t l = 0; l + 1 < off.size(); ++l) {
       a.level_nodes = nodes + off[l];
+      a.level_desc = desc + off[l];
       a.n_level = off[l + 1] - off[l];
       e = post ? launch_post_level<T>(a, ctx->L.SP, ctx->L.RP, st)
                : launch_pre_level<T>(a, ctx->L.SP, ctx->L.RP, st);
@@ -310,8 +323,38 @@ int capture(phylo_ctx* ctx, int first, int last, cudaGraphExec_t* exec) {
   return PHYLO_OK;
 }
 
+template <typename T>
+int upload(phylo_ctx* ctx, const Region& r, const T* host, size_t count,
+           const char* what);
+
+// Level-node descriptors {k, child 0, child 1, flags} for both passes; the
+// flags depend on which tips carry partial vectors.
+int upload_descriptors(phylo_ctx* ctx) {
+  for (int pass = 0; pass < 2; ++pass) {
+    const std::vector<int>& nodes = pass == 0 ? ctx->post_nodes : ctx->pre_nodes;
+    std::vector<int4> desc(nodes.size());
+    for (size_t i = 0; i < nodes.size(); ++i) {
+      const int k = nodes[i];
+      const int2 ch = ctx->children[k];
+      int flags = 0;
+      if (ch.x < ctx->N && !ctx->tip_has[ch.x]) flags |= kDescFlagCompact0;
+      if (ch.y < ctx->N && !ctx->tip_has[ch.y]) flags |= kDescFlagCompact1;
+      desc[i] = make_int4(k, ch.x, ch.y, flags);
+    }
+    if (!desc.empty()) {
+      int rc = upload(ctx, pass == 0 ? ctx->L.post_desc : ctx->L.pre_desc, desc.data(),
+                      desc.size(), "upload level descriptors");
+      if (rc) return rc;
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    }
+  }
+  return PHYLO_OK;
+}
+
 int build_graph(phylo_ctx* ctx) {
   int rc = ensure_cuda_objects(ctx);
+  if (rc) return rc;
+  rc = upload_descriptors(ctx);
   if (rc) return rc;
   invalidate_graph(ctx);
   rc = capture(ctx, 0, kPhases - 1, &ctx->gexec);
@@ -322,6 +365,8 @@ int build_graph(phylo_ctx* ctx) {
 
 int build_phase_graphs(phylo_ctx* ctx) {
   int rc = ensure_cuda_objects(ctx);
+  if (rc) return rc;
+  rc = upload_descriptors(ctx);
   if (rc) return rc;
   for (int ph = 0; ph < kPhases; ++ph) {
     if (ctx->phase_exec[ph]) cudaGraphExecDestroy(ctx->phase_exec[ph]);
@@ -361,6 +406,8 @@ int launch_eval(phylo_ctx* ctx) {
 
 int read_flags(phylo_ctx* ctx, int flags) {
   if (flags == 0) return PHYLO_OK;
+  if (flags & ERR_TIMEOUT)
+    return fail(ctx, PHYLO_ETIMEOUT, "device flagged: a bounded wait on an asynchronous copy expired");
   return fail(ctx, PHYLO_ENUMERIC,
               "device flagged:%s%s%s", (flags & ERR_ZERO_PARTIAL) ? " zero-or-nonfinite-partial" : "",
               (flags & ERR_BAD_LENGTH) ? " bad-branch-length" : "",
@@ -420,6 +467,23 @@ int upload(phylo_ctx* ctx, const Region& r, const T* host, size_t count,
   CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws + r.off, host, count * sizeof(T),
                                 cudaMemcpyHostToDevice, ctx->stream),
            what);
+  return PHYLO_OK;
+}
+
+// Upload FP64 host values into a region of the path's element type
+// (synchronous: the converted copy is a local buffer).
+int upload_typed(phylo_ctx* ctx, const Region& r, const double* host, size_t count,
+                 const char* what) {
+  if (!count) return PHYLO_OK;
+  if (ctx->precision == PHYLO_FP64) {
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws + r.off, host, count * 8, cudaMemcpyHostToDevice,
+                                  ctx->stream), what);
+  } else {
+    std::vector<float> buf(host, host + count);
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->ws + r.off, buf.data(), count * 4,
+                                  cudaMemcpyHostToDevice, ctx->stream), what);
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  }
   return PHYLO_OK;
 }
 
@@ -561,9 +625,11 @@ int phylo_set_tip_states(phylo_ctx* ctx, const uint8_t* states) {
       return fail(ctx, PHYLO_EINVAL, "tip %zu pattern %zu: state %d > n_states %d",
                   i / (ctx->C ? ctx->C : 1), i % (ctx->C ? ctx->C : 1),
                   (int)states[i], ctx->S);
-  if (n) {
-    int rc = upload(ctx, ctx->L.tip_states, states, n, "upload tip states");
-    if (rc) return rc;
+  if (n) {  // rows padded to 16 bytes for the bulk copies
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->ws + ctx->L.tip_states.off, round_up(ctx->C, 16),
+                                    states, ctx->C, ctx->C, ctx->N, cudaMemcpyHostToDevice,
+                                    ctx->stream),
+             "upload tip states");
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }
   ctx->have_states = true;
@@ -624,6 +690,8 @@ int phylo_set_pattern_weights(phylo_ctx* ctx, const double* w) {
       return fail(ctx, PHYLO_EINVAL, "pattern weight %d must be finite and >= 0", c);
   if (ctx->C) {
     int rc = upload(ctx, ctx->L.pattern_w, w, ctx->C, "upload pattern weights");
+    if (rc) return rc;
+    rc = upload_typed(ctx, ctx->L.pattern_wt, w, ctx->C, "upload pattern weights");
     if (rc) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }
@@ -743,6 +811,7 @@ int phylo_set_categories(phylo_ctx* ctx, const double* rates, const double* weig
   int rc;
   if ((rc = upload(ctx, ctx->L.rates, rates, (size_t)ctx->R, "upload rates"))) return rc;
   if ((rc = upload(ctx, ctx->L.cat_w, weights, (size_t)ctx->R, "upload weights"))) return rc;
+  if ((rc = upload_typed(ctx, ctx->L.cat_wt, weights, (size_t)ctx->R, "upload weights"))) return rc;
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   ctx->have_cats = true;
   return PHYLO_OK;

@@ -9,12 +9,19 @@
 
 namespace phylo {
 
+// Flags of a level-node descriptor: child 0 / child 1 is a tip with a
+// compact state.
+constexpr int kDescFlagCompact0 = 1, kDescFlagCompact1 = 2;
+
 // Device-side numeric flags (bit mask in the workspace's error word).
 enum : int {
   ERR_ZERO_PARTIAL = 1,  // a partial vector was all zero / NaN for a pattern
   ERR_BAD_LENGTH = 2,    // a branch length was negative or not finite
-  ERR_BAD_RATIO = 4      // a gradient denominator was zero or not finite
+  ERR_BAD_RATIO = 4,     // a gradient denominator was zero or not finite
+  ERR_TIMEOUT = 8        // a bounded wait on an asynchronous copy expired
 };
+
+__host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // Padded state count used by the kernels for a model with S states.
 inline int padded_states(int S) {
@@ -37,8 +44,13 @@ constexpr int kWideThreads = 256;
 constexpr int kWidePatternsF32 = 16;
 constexpr int kWidePatternsF64 = 8;
 
-// Patterns handled by one thread block of a level kernel.
+// Patterns per block of the FP32 4-state kernels (kernels_p4.cuh), one
+// thread per pattern.
+constexpr int kP4TilePatterns = 64;
+
+// Patterns of one tile (the unit of the per-tile gradient sums).
 inline int patterns_per_tile(int SP, int R, bool fp64) {
+  if (SP == 4 && !fp64) return kP4TilePatterns;
   if (SP <= 20) return kSmallThreads / lanes_per_pattern(R);
   return fp64 ? kWidePatternsF64 : kWidePatternsF32;
 }
@@ -50,19 +62,24 @@ template <typename T>
 struct LevelArgs {
   const int2* children;        // [2N-1]; (-1,-1) for tips
   const int* level_nodes;      // internal nodes of this level
+  const int4* level_desc;      // per level node: {k, child 0, child 1, flags}
   int n_level;                 // number of nodes in the level
   int n_tips, n_patterns, n_states, n_cat, root;
   const T* P;                  // [2N-2][R][SP][SP], row = parent state
   const T* dP;                 // same layout: dP/dt = gamma_r Q P
   T* post;                     // [N-1][C][R][SP] post-order partials
   T* pre;                      // [N-1][C][R][SP] pre-order partials
-  int* escale;                 // [N-1][C] cumulative post-order exponents
-  const uint8_t* tip_states;   // [N][C]; value S = gap
+  int* escale;                 // [N-1][escale_stride] cumulative exponents
+  const uint8_t* tip_states;   // [N][state_stride]; value S = gap
+  int state_stride;            // C rounded up to 16 (16-byte rows)
+  int escale_stride;           // C rounded up to 4 (16-byte rows)
   const T* tip_partials;       // [N][C][SP] or nullptr
   const int* tip_has_partials; // [N] or nullptr
   const double* pattern_w;     // [C]
   const double* root_pi;       // [S]
   const double* cat_w;         // [R]
+  const T* pattern_wt;         // [C] the same weights in T
+  const T* cat_wt;             // [R] the same weights in T
   double* gpart;               // [2N-2][n_tiles] per-tile gradient sums
   double* lpart;               // [n_tiles] per-tile log-likelihood sums
   int n_tiles;

@@ -56,9 +56,9 @@ struct NaRegion {
 
 struct NaLayout {
   int SP = 0, RP = 0, n_tiles = 0;
-  NaRegion children, post_nodes, pre_nodes, P, dP, post, pre, escale;
+  NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale;
   NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
-  NaRegion gpart, lpart, out;
+  NaRegion gpart, lpart, out, pattern_wt, cat_wt;
   size_t total = 0;
 };
 
@@ -82,12 +82,14 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.children, n_nodes * sizeof(int2));
   na_add(L, L.post_nodes, n_int * sizeof(int));
   na_add(L, L.pre_nodes, n_int * sizeof(int));
+  na_add(L, L.post_desc, n_int * sizeof(int4));
+  na_add(L, L.pre_desc, n_int * sizeof(int4));
   na_add(L, L.P, mat);
   na_add(L, L.dP, mat);
   na_add(L, L.post, part);
   na_add(L, L.pre, part);
-  na_add(L, L.escale, n_int * (size_t)C * sizeof(int));
-  na_add(L, L.tip_states, (size_t)N * C);
+  na_add(L, L.escale, n_int * (size_t)round_up(C, 4) * sizeof(int));
+  na_add(L, L.tip_states, (size_t)N * round_up(C, 16));
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
   na_add(L, L.Vinv, (size_t)S * S * 8);
@@ -99,6 +101,8 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.gpart, n_br * (size_t)L.n_tiles * 8);
   na_add(L, L.lpart, (size_t)L.n_tiles * 8);
   na_add(L, L.out, n_nodes * 8 + 8);
+  na_add(L, L.pattern_wt, (size_t)C * sizeof(float));
+  na_add(L, L.cat_wt, (size_t)R * sizeof(float));
   *Lp = L;
 }
 
@@ -123,6 +127,17 @@ int scratch_for_current_device(void** out) {
   }
   *out = g_scratch_ptr[dev];
   return PHYLO_OK;
+}
+
+__global__ void to_float_kernel(const double* __restrict__ src, float* dst, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+
+cudaError_t launch_to_float(const double* src, float* dst, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  to_float_kernel<<<(n + 255) / 256, 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
 }
 
 #define NA_TRY(call, what)                                                      \
@@ -252,7 +267,26 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   NA_TRY(up(L.children, ch, n * sizeof(int2)), "upload tree");
   NA_TRY(up(L.post_nodes, post_nodes, (size_t)post_off[n_post] * sizeof(int)), "upload schedule");
   NA_TRY(up(L.pre_nodes, pre_nodes, (size_t)pre_off[n_pre] * sizeof(int)), "upload schedule");
-  NA_TRY(up(L.tip_states, tip_states, (size_t)N * C), "upload tip states");
+  {  // level-node descriptors {k, child 0, child 1, flags}; every tip is compact
+    int4 desc[kMaxNoAllocTips];
+    for (int pass = 0; pass < 2; ++pass) {
+      const int* nodes = pass == 0 ? post_nodes : pre_nodes;
+      const int count = pass == 0 ? post_off[n_post] : pre_off[n_pre];
+      for (int i = 0; i < count; ++i) {
+        const int2 c2 = ch[nodes[i]];
+        desc[i] = make_int4(nodes[i], c2.x, c2.y,
+                            (c2.x < N ? kDescFlagCompact0 : 0) | (c2.y < N ? kDescFlagCompact1 : 0));
+      }
+      NA_TRY(up(pass == 0 ? L.post_desc : L.pre_desc, desc, (size_t)count * sizeof(int4)),
+             "upload descriptors");
+      // the host array is reused: finish this copy first
+      NA_TRY(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+    }
+  }
+  if (C)
+    NA_TRY(cudaMemcpy2DAsync(ws + L.tip_states.off, round_up(C, 16), tip_states, C, C, N,
+                             cudaMemcpyHostToDevice, st),
+           "upload tip states");
   NA_TRY(up(L.pattern_w, pattern_weights, (size_t)C * 8), "upload weights");
   NA_TRY(up(L.V, V, (size_t)S * S * 8), "upload V");
   NA_TRY(up(L.Vinv, Vinv, (size_t)S * S * 8), "upload Vinv");
@@ -261,6 +295,13 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   NA_TRY(up(L.rates, rates, (size_t)R * 8), "upload rates");
   NA_TRY(up(L.cat_w, cat_weights, (size_t)R * 8), "upload weights");
   NA_TRY(up(L.t, branch_lengths, (2 * (size_t)N - 2) * 8), "upload branch lengths");
+  // FP32 copies of the weights, converted on the GPU (no host buffer)
+  NA_TRY(launch_to_float(reinterpret_cast<const double*>(ws + L.pattern_w.off),
+                         reinterpret_cast<float*>(ws + L.pattern_wt.off), C, st),
+         "convert weights");
+  NA_TRY(launch_to_float(reinterpret_cast<const double*>(ws + L.cat_w.off),
+                         reinterpret_cast<float*>(ws + L.cat_wt.off), R, st),
+         "convert weights");
   // The scratch keeps the previous call's contents: the flag word is the
   // only location read before this call writes it.
   int* flag = reinterpret_cast<int*>(ws + L.out.off + (2 * (size_t)N - 1) * 8);
@@ -292,24 +333,32 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   a.pre = reinterpret_cast<float*>(ws + L.pre.off);
   a.escale = reinterpret_cast<int*>(ws + L.escale.off);
   a.tip_states = reinterpret_cast<const uint8_t*>(ws + L.tip_states.off);
+  a.state_stride = round_up(C, 16);
+  a.escale_stride = round_up(C, 4);
   a.tip_partials = nullptr;
   a.tip_has_partials = nullptr;
   a.pattern_w = reinterpret_cast<const double*>(ws + L.pattern_w.off);
   a.root_pi = reinterpret_cast<const double*>(ws + L.pi.off);
   a.cat_w = reinterpret_cast<const double*>(ws + L.cat_w.off);
+  a.pattern_wt = reinterpret_cast<const float*>(ws + L.pattern_wt.off);
+  a.cat_wt = reinterpret_cast<const float*>(ws + L.cat_wt.off);
   a.gpart = reinterpret_cast<double*>(ws + L.gpart.off);
   a.lpart = reinterpret_cast<double*>(ws + L.lpart.off);
   a.n_tiles = L.n_tiles;
   a.err = flag;
   const int* dpost = reinterpret_cast<const int*>(ws + L.post_nodes.off);
   const int* dpre = reinterpret_cast<const int*>(ws + L.pre_nodes.off);
+  const int4* dpostd = reinterpret_cast<const int4*>(ws + L.post_desc.off);
+  const int4* dpred = reinterpret_cast<const int4*>(ws + L.pre_desc.off);
   for (int l = 0; l < n_post; ++l) {
     a.level_nodes = dpost + post_off[l];
+    a.level_desc = dpostd + post_off[l];
     a.n_level = post_off[l + 1] - post_off[l];
     NA_TRY(launch_post_level<float>(a, L.SP, L.RP, st), "post-order level");
   }
   for (int l = 0; l < n_pre; ++l) {
     a.level_nodes = dpre + pre_off[l];
+    a.level_desc = dpred + pre_off[l];
     a.n_level = pre_off[l + 1] - pre_off[l];
     NA_TRY(launch_pre_level<float>(a, L.SP, L.RP, st), "pre-order level");
   }
