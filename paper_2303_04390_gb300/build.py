@@ -22,6 +22,8 @@ HEADERS = ["phylo_internal.h", "kernels.cuh", "kernels_p4.cuh", "tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-Wall"]
+# extra compile flags (e.g. -DPHYLO_P4_TILE=128 to retune a kernel)
+FLAGS += os.environ.get("PHYLO_NVCC_FLAGS", "").split()
 
 
 def _nvcc():

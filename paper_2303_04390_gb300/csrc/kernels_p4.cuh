@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
     // Eq. 3 at the root: L_c = sum_r w_r pi' p_root,r,c, exponents restored
     double term = 0.0;
     if (valid) {
-      const float2 pl = make_float2((float)a.root_pi[0], S > 1 ? (float)a.root_pi[1] : 0.f);
-      const float2 ph = make_float2(S > 2 ? (float)a.root_pi[2] : 0.f, S > 3 ? (float)a.root_pi[3] : 0.f);
+      const float2 pl = make_float2(a.root_pit[0], S > 1 ? a.root_pit[1] : 0.f);
+      const float2 ph = make_float2(S > 2 ? a.root_pit[2] : 0.f, S > 3 ? a.root_pit[3] : 0.f);
       float L = 0.f;
 #pragma unroll
       for (int r = 0; r < RM; ++r)
@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
   // ---- Eq. 4 and Eq. 8: children's pre-order partials and the ratio ------
   float2 rootlo = make_float2(0.f, 0.f), roothi = rootlo;
   if (k == a.root) {
-    rootlo = make_float2((float)a.root_pi[0], S > 1 ? (float)a.root_pi[1] : 0.f);
-    roothi = make_float2(S > 2 ? (float)a.root_pi[2] : 0.f, S > 3 ? (float)a.root_pi[3] : 0.f);
+    rootlo = make_float2(a.root_pit[0], S > 1 ? a.root_pit[1] : 0.f);
+    roothi = make_float2(S > 2 ? a.root_pit[2] : 0.f, S > 3 ? a.root_pit[3] : 0.f);
   }
   const bool int_i = bi >= a.n_tips, int_j = bj >= a.n_tips;
   float2 qilo[RM], qihi[RM], qjlo[RM], qjhi[RM];

@@ -39,7 +39,7 @@ struct Layout {
   Region P, dP, post, pre, escale;
   Region tip_states, tip_partials, tip_has;
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
-  Region pattern_wt, cat_wt;  // the weights in the path's element type
+  Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
   Region gpart, lpart, out;  // out = [logL, grad...] followed by the flag word
   size_t total = 0;
 };
@@ -108,6 +108,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.cat_w, (size_t)R * 8);
   ok &= add_region(L, L.pattern_wt, (size_t)C * L.elem);
   ok &= add_region(L, L.cat_wt, (size_t)R * L.elem);
+  ok &= add_region(L, L.pi_t, (size_t)S * L.elem);
   ok &= add_region(L, L.t, n_br * 8);
   if (!mul_ok(n_br, (size_t)L.n_tiles * 8, &tmp)) return "size overflow";
   ok &= add_region(L, L.gpart, tmp);
@@ -212,6 +213,7 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.cat_w = ctx->dev<double>(ctx->L.cat_w);
   a.pattern_wt = ctx->dev<T>(ctx->L.pattern_wt);
   a.cat_wt = ctx->dev<T>(ctx->L.cat_wt);
+  a.root_pit = ctx->dev<T>(ctx->L.pi_t);
   a.gpart = ctx->dev<double>(ctx->L.gpart);
   a.lpart = ctx->dev<double>(ctx->L.lpart);
   a.n_tiles = ctx->L.n_tiles;
@@ -727,6 +729,7 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
   if ((rc = upload(ctx, ctx->L.Vinv, Vinv, (size_t)S * S, "upload Vinv"))) return rc;
   if ((rc = upload(ctx, ctx->L.lambda, lambda, (size_t)S, "upload lambda"))) return rc;
   if ((rc = upload(ctx, ctx->L.pi, pi, (size_t)S, "upload pi"))) return rc;
+  if ((rc = upload_typed(ctx, ctx->L.pi_t, pi, (size_t)S, "upload pi"))) return rc;
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   ctx->have_eigen = true;
   return PHYLO_OK;

@@ -46,7 +46,10 @@ constexpr int kWidePatternsF64 = 8;
 
 // Patterns per block of the FP32 4-state kernels (kernels_p4.cuh), one
 // thread per pattern.
-constexpr int kP4TilePatterns = 64;
+#ifndef PHYLO_P4_TILE
+#define PHYLO_P4_TILE 64
+#endif
+constexpr int kP4TilePatterns = PHYLO_P4_TILE;
 
 // Patterns of one tile (the unit of the per-tile gradient sums).
 inline int patterns_per_tile(int SP, int R, bool fp64) {
@@ -80,6 +83,7 @@ struct LevelArgs {
   const double* cat_w;         // [R]
   const T* pattern_wt;         // [C] the same weights in T
   const T* cat_wt;             // [R] the same weights in T
+  const T* root_pit;           // [S] the root distribution in T
   double* gpart;               // [2N-2][n_tiles] per-tile gradient sums
   double* lpart;               // [n_tiles] per-tile log-likelihood sums
   int n_tiles;

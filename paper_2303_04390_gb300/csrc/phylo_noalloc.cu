@@ -58,7 +58,7 @@ struct NaLayout {
   int SP = 0, RP = 0, n_tiles = 0;
   NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale;
   NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
-  NaRegion gpart, lpart, out, pattern_wt, cat_wt;
+  NaRegion gpart, lpart, out, pattern_wt, cat_wt, pi_t;
   size_t total = 0;
 };
 
@@ -103,6 +103,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.out, n_nodes * 8 + 8);
   na_add(L, L.pattern_wt, (size_t)C * sizeof(float));
   na_add(L, L.cat_wt, (size_t)R * sizeof(float));
+  na_add(L, L.pi_t, (size_t)S * sizeof(float));
   *Lp = L;
 }
 
@@ -302,6 +303,9 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   NA_TRY(launch_to_float(reinterpret_cast<const double*>(ws + L.cat_w.off),
                          reinterpret_cast<float*>(ws + L.cat_wt.off), R, st),
          "convert weights");
+  NA_TRY(launch_to_float(reinterpret_cast<const double*>(ws + L.pi.off),
+                         reinterpret_cast<float*>(ws + L.pi_t.off), S, st),
+         "convert pi");
   // The scratch keeps the previous call's contents: the flag word is the
   // only location read before this call writes it.
   int* flag = reinterpret_cast<int*>(ws + L.out.off + (2 * (size_t)N - 1) * 8);
@@ -342,6 +346,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   a.cat_w = reinterpret_cast<const double*>(ws + L.cat_w.off);
   a.pattern_wt = reinterpret_cast<const float*>(ws + L.pattern_wt.off);
   a.cat_wt = reinterpret_cast<const float*>(ws + L.cat_wt.off);
+  a.root_pit = reinterpret_cast<const float*>(ws + L.pi_t.off);
   a.gpart = reinterpret_cast<double*>(ws + L.gpart.off);
   a.lpart = reinterpret_cast<double*>(ws + L.lpart.off);
   a.n_tiles = L.n_tiles;
