@@ -16,6 +16,8 @@ Printed as one JSON line:
              against the measured HBM copy bandwidth
   fp64_path  the plain FP64 path on the same workload and GPU
   cpu_baseline the FP64 oracle on the host (bounded pattern sample)
+  served     the continuous-batching request loop on a Poisson stream of
+             independent requests (p50/p99 latency, evals/s)
 
 --impl reference times the oracle as the reference arm.
 Under torchrun each rank runs an independent replica (weak scaling, no
@@ -264,6 +266,47 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
+def run_served(args, seed=0):
+    """Served stream: requests drawn from a pool of distinct seeded
+    problems (Yule trees with 16-2,048 taxa, 100-20,000 patterns, 4 or 20
+    states), first all at once (closed loop, to measure throughput mu),
+    then as a Poisson stream at 0.7 mu."""
+    import synth
+    from paper_2303_04390_gb300.serve import (Server, latency_summary,
+                                              poisson_arrivals)
+    pool = [synth.served_request(k, seed) for k in range(args.serve_pool)]
+    n = args.serve_requests
+    reqs = [pool[k % len(pool)] for k in range(n)]
+    budget = int(args.serve_budget_gb * (1 << 30))
+    srv = Server(memory_budget_bytes=budget, max_active=32, n_streams=16,
+                 setup_workers=6)
+    srv.run(reqs[:min(n, 2 * len(pool))])  # warm-up: every pool entry
+    n_closed = min(n, 1024)
+    t0 = time.perf_counter()
+    res = srv.run(reqs[:n_closed])
+    closed = latency_summary(res, time.perf_counter() - t0)
+    rate = 0.7 * closed["evals_per_s"]
+    arrivals = poisson_arrivals(n, rate, seed=seed + 1)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, arrivals)
+    open_loop = latency_summary(res, time.perf_counter() - t0)
+    srv.close()
+    return {
+        "requests": n, "distinct_problems": len(pool),
+        "arrival": f"Poisson at 0.7 x closed-loop throughput "
+                   f"({rate:.1f}/s)",
+        "evals_per_s": open_loop["evals_per_s"],
+        "p50_ms": open_loop["p50_ms"], "p99_ms": open_loop["p99_ms"],
+        "max_ms": open_loop["max_ms"], "failed": open_loop["failed"],
+        "closed_loop_evals_per_s": closed["evals_per_s"],
+        "closed_loop_p50_ms": closed["p50_ms"],
+        "closed_loop_p99_ms": closed["p99_ms"],
+        "budget_gb": args.serve_budget_gb,
+        "peak_resident_gb": srv.admission.peak_used / (1 << 30),
+        "peak_active": srv.admission.peak_active,
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -437,6 +480,9 @@ def run_ours(args):
         "launches_per_evaluation": n_launch_dom,
         "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
     }
+    served = None
+    if not args.skip_serve:
+        served = run_served(args)
     cpu = None
     if world == 1 and not args.skip_cpu:
         cpu = cpu_baseline(args.workload)
@@ -467,6 +513,7 @@ def run_ours(args):
         "phases": phases,
         "hbm_gbs_all_phases": sum(by.values()) / (ms / K / 1e3) / 1e9,
         "fp64_path": fp64,
+        "served": served,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
@@ -489,6 +536,10 @@ def main():
                     help="override the workload's number of tips")
     ap.add_argument("--patterns", type=int, default=None,
                     help="override the workload's number of patterns")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-pool", type=int, default=96)
+    ap.add_argument("--serve-budget-gb", type=float, default=32.0)
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up + K evaluations only (profiler target)")
     args = ap.parse_args()

@@ -57,7 +57,10 @@ enum phylo_precision {
 };
 
 enum phylo_flags {
-  PHYLO_FLAG_TIP_PARTIALS = 1 /* reserve storage so tips may carry partials */
+  PHYLO_FLAG_TIP_PARTIALS = 1, /* reserve storage so tips may carry partials */
+  PHYLO_FLAG_NO_GRAPH = 2      /* launch kernels directly, no CUDA graph
+                                  (one-shot contexts: capture would cost
+                                  more than it saves) */
 };
 
 /* Bytes of device workspace a context of this shape needs.  Host only.
@@ -148,6 +151,18 @@ int phylo_evaluate_device(phylo_ctx* ctx, double* out);
  * so per-phase device times can be read with cudaEventElapsedTime. */
 int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out,
                                 void* const* events);
+
+/* The evaluation split at its natural seam, for reverse-mode use (the
+ * pre-order pass is the backward of the post-order pass): forward runs the
+ * matrix build, the post-order pass and the log-likelihood reduction and
+ * writes log P(Y) (1 FP64 value) to the device pointer `out`; backward runs
+ * the pre-order pass with the fused gradient and the gradient reduction
+ * and writes d log P(Y)/d t (2N-2 FP64 values) to the device pointer `out`.
+ * Both are asynchronous on the stream.  Backward returns PHYLO_ESTATE
+ * unless a forward (or a full evaluation) ran since the last change of the
+ * branch lengths. */
+int phylo_forward_device(phylo_ctx* ctx, double* out);
+int phylo_backward_device(phylo_ctx* ctx, double* out);
 
 /* Synchronise the stream and report device-side numeric flags raised since
  * the last check (PHYLO_ENUMERIC) or PHYLO_OK. */

@@ -22,6 +22,7 @@ PHYLO_ETIMEOUT = -6
 PHYLO_FP64 = 0
 PHYLO_FP32 = 1
 PHYLO_FLAG_TIP_PARTIALS = 1
+PHYLO_FLAG_NO_GRAPH = 2
 
 _c_int = ctypes.c_int
 _c_size = ctypes.c_size_t
@@ -49,6 +50,8 @@ SIGNATURES = {
     "phylo_evaluate_device": (_c_int, [_vp, _vp]),
     "phylo_evaluate_device_timed": (_c_int, [_vp, _vp,
                                              ctypes.POINTER(_vp)]),
+    "phylo_forward_device": (_c_int, [_vp, _vp]),
+    "phylo_backward_device": (_c_int, [_vp, _vp]),
     "phylo_check": (_c_int, [_vp]),
     "phylo_launches_per_evaluation": (_c_int, [_vp]),
     "phylo_level_counts": (_c_int, [_vp, ctypes.POINTER(_c_int),

@@ -57,7 +57,7 @@ class PhyloContext:
 
     def __init__(self, n_tips: int, n_patterns: int, n_states: int,
                  n_categories: int, precision="fp32", tip_partials=False,
-                 device=None, stream=None):
+                 device=None, stream=None, use_graph=True):
         import torch
         self._lib = N.load()
         self.n_tips, self.n_patterns = n_tips, n_patterns
@@ -76,11 +76,12 @@ class PhyloContext:
         self.stream = stream
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
         ctx = ctypes.c_void_p()
+        flags = (N.PHYLO_FLAG_TIP_PARTIALS if tip_partials else 0) | \
+            (0 if use_graph else N.PHYLO_FLAG_NO_GRAPH)
         rc = self._lib.phylo_create(
             ctypes.byref(ctx), n_tips, n_patterns, n_states, n_categories,
-            _prec(precision),
-            N.PHYLO_FLAG_TIP_PARTIALS if tip_partials else 0,
-            ctypes.c_void_p(ptr), nbytes, ctypes.c_void_p(sp))
+            _prec(precision), flags, ctypes.c_void_p(ptr), nbytes,
+            ctypes.c_void_p(sp))
         N.check(rc)
         self._ctx = ctx
         self._out = None
@@ -228,12 +229,13 @@ class PhyloContext:
 
 
 def from_workload(w, precision: Optional[str] = None, device=None,
-                  stream=None, tip_partials=False) -> PhyloContext:
+                  stream=None, tip_partials=False,
+                  use_graph=True) -> PhyloContext:
     """Context with every input of a synth.Workload set (branch lengths
     included)."""
     ctx = PhyloContext(w.n_tips, w.n_patterns, w.n_states, w.n_categories,
                        precision or w.precision, tip_partials=tip_partials,
-                       device=device, stream=stream)
+                       device=device, stream=stream, use_graph=use_graph)
     ctx.set_tree(w.parent)
     ctx.set_tip_states(w.tip_states)
     ctx.set_pattern_weights(w.pattern_weights)

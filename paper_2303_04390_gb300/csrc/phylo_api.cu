@@ -65,7 +65,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   if (S < 2 || S > 64) return "n_states must be in [2, 64]";
   if (R < 1 || R > 8) return "n_categories must be in [1, 8]";
   if (prec != PHYLO_FP64 && prec != PHYLO_FP32) return "unknown precision";
-  if (flags & ~PHYLO_FLAG_TIP_PARTIALS) return "unknown flags";
+  if (flags & ~(PHYLO_FLAG_TIP_PARTIALS | PHYLO_FLAG_NO_GRAPH)) return "unknown flags";
   Layout L;
   L.SP = padded_states(S);
   L.RP = lanes_per_pattern(R);
@@ -132,6 +132,9 @@ struct phylo_ctx {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t gexec = nullptr;
   cudaGraphExec_t phase_exec[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t fwd_exec = nullptr;  // matrices + post-order + logL reduction
+  cudaGraphExec_t bwd_exec = nullptr;  // pre-order + gradient reduction
+  bool forward_valid = false;          // post-order partials match the inputs
   bool graph_dirty = true;
   bool phase_dirty = true;
   bool prepared = false;
@@ -183,8 +186,12 @@ void invalidate_graph(phylo_ctx* ctx) {
     if (g) cudaGraphExecDestroy(g);
     g = nullptr;
   }
+  if (ctx->fwd_exec) cudaGraphExecDestroy(ctx->fwd_exec);
+  if (ctx->bwd_exec) cudaGraphExecDestroy(ctx->bwd_exec);
+  ctx->fwd_exec = ctx->bwd_exec = nullptr;
   ctx->graph_dirty = true;
   ctx->phase_dirty = true;
+  ctx->forward_valid = false;
 }
 
 template <typename T>
@@ -227,8 +234,10 @@ int* flag_word(const phylo_ctx* ctx) {
 
 // Phases of one evaluation: 0 = flag reset + matrices (Eq. 1), 1 = post-order
 // levels (Eqs. 2-3), 2 = pre-order levels with the gradient (Eqs. 4, 8),
-// 3 = final reduction (Eq. 7).
+// 3 = final reduction (Eq. 7).  Phase 4 (not part of an evaluation) is the
+// log-likelihood reduction alone, which ends the forward pass.
 constexpr int kPhases = 4;
+constexpr int kPhaseLogLOnly = 4;
 
 template <typename T>
 cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
@@ -270,13 +279,14 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
   ra.gpart = ctx->dev<double>(ctx->L.gpart);
   ra.lpart = ctx->dev<double>(ctx->L.lpart);
   ra.n_tiles = ctx->L.n_tiles;
-  ra.n_branches = 2 * ctx->N - 2;
+  ra.n_branches = phase == kPhaseLogLOnly ? 0 : 2 * ctx->N - 2;
   ra.out = ctx->dev<double>(ctx->L.out);
   return launch_reduce(ra, st);
 }
 
 cudaError_t enqueue_phases(phylo_ctx* ctx, int first, int last, cudaStream_t st) {
   for (int ph = first; ph <= last; ++ph) {
+    if (ph == kPhases) continue;  // (no phase between the reduction forms)
     cudaError_t e = ctx->precision == PHYLO_FP64 ? enqueue_phase<double>(ctx, ph, st)
                                                  : enqueue_phase<float>(ctx, ph, st);
     if (e != cudaSuccess) return e;
@@ -292,9 +302,20 @@ int ensure_cuda_objects(phylo_ctx* ctx) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel attributes");
     ctx->prepared = true;
   }
+  return PHYLO_OK;
+}
+
+// The private stream that CUDA graphs are captured on (created on first
+// capture; a context that never captures never creates it).
+int ensure_capture_stream(phylo_ctx* ctx) {
   if (!ctx->cap_stream)
     CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
              "cudaStreamCreate");
+  return PHYLO_OK;
+}
+
+// Pinned staging for results read back to the host (first host read-back).
+int ensure_host_out(phylo_ctx* ctx) {
   if (!ctx->host_out) {
     void* p = nullptr;
     CUDA_TRY(ctx, cudaHostAlloc(&p, (2 * (size_t)ctx->N - 1) * 8 + 8, cudaHostAllocDefault),
@@ -306,6 +327,8 @@ int ensure_cuda_objects(phylo_ctx* ctx) {
 
 // Capture phases [first, last] into an executable graph.
 int capture(phylo_ctx* ctx, int first, int last, cudaGraphExec_t* exec) {
+  int rc = ensure_capture_stream(ctx);
+  if (rc) return rc;
   CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal),
            "cudaStreamBeginCapture");
   cudaError_t le = enqueue_phases(ctx, first, last, ctx->cap_stream);
@@ -350,6 +373,31 @@ int upload_descriptors(phylo_ctx* ctx) {
       CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     }
   }
+  return PHYLO_OK;
+}
+
+// Run phases [first, last] on the context's stream: replayed from a cached
+// graph, or launched directly when the context was created with
+// PHYLO_FLAG_NO_GRAPH (one-shot contexts, where capture would cost more
+// than it saves).
+int run_phases(phylo_ctx* ctx, int first, int last, cudaGraphExec_t* cache) {
+  int rc = ensure_cuda_objects(ctx);
+  if (rc) return rc;
+  if (ctx->graph_dirty || ctx->phase_dirty) {
+    rc = upload_descriptors(ctx);
+    if (rc) return rc;
+  }
+  if (ctx->flags & PHYLO_FLAG_NO_GRAPH) {
+    cudaError_t e = enqueue_phases(ctx, first, last, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel launch");
+    ctx->graph_dirty = ctx->phase_dirty = false;
+    return PHYLO_OK;
+  }
+  if (!*cache) {
+    rc = capture(ctx, first, last, cache);
+    if (rc) return rc;
+  }
+  CUDA_TRY(ctx, cudaGraphLaunch(*cache, ctx->stream), "cudaGraphLaunch");
   return PHYLO_OK;
 }
 
@@ -398,11 +446,18 @@ int check_ready(phylo_ctx* ctx) {
 int launch_eval(phylo_ctx* ctx) {
   int rc = check_ready(ctx);
   if (rc) return rc;
+  if (ctx->flags & PHYLO_FLAG_NO_GRAPH) {
+    rc = run_phases(ctx, 0, kPhases - 1, nullptr);
+    if (rc) return rc;
+    ctx->forward_valid = true;
+    return PHYLO_OK;
+  }
   if (ctx->graph_dirty || !ctx->gexec) {
     rc = build_graph(ctx);
     if (rc) return rc;
   }
   CUDA_TRY(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream), "cudaGraphLaunch");
+  ctx->forward_valid = true;
   return PHYLO_OK;
 }
 
@@ -834,6 +889,7 @@ int phylo_set_branch_lengths(phylo_ctx* ctx, const double* t, int on_device) {
                                 ctx->stream),
            "upload branch lengths");
   ctx->have_t = true;
+  ctx->forward_valid = false;
   return PHYLO_OK;
 }
 
@@ -841,6 +897,8 @@ int phylo_evaluate(phylo_ctx* ctx, double* logL, double* grad) {
   if (!ctx) return PHYLO_EINVAL;
   if (!logL) return fail(ctx, PHYLO_EINVAL, "log_likelihood is NULL");
   int rc = launch_eval(ctx);
+  if (rc) return rc;
+  rc = ensure_host_out(ctx);
   if (rc) return rc;
   const size_t n = 2 * (size_t)ctx->N - 1;
   CUDA_TRY(ctx, cudaMemcpyAsync(ctx->host_out, ctx->dev<double>(ctx->L.out), n * 8 + 8,
@@ -876,7 +934,7 @@ int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out, void* const* events
     if (!events[i]) return fail(ctx, PHYLO_EINVAL, "event %d is NULL", i);
   int rc = check_ready(ctx);
   if (rc) return rc;
-  if (ctx->phase_dirty) {
+  if (ctx->phase_dirty || !ctx->phase_exec[0]) {
     rc = build_phase_graphs(ctx);
     if (rc) return rc;
   }
@@ -892,6 +950,50 @@ int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out, void* const* events
     CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->dev<double>(ctx->L.out), n * 8,
                                   cudaMemcpyDeviceToDevice, ctx->stream),
              "copy results");
+  return PHYLO_OK;
+}
+
+int phylo_forward_device(phylo_ctx* ctx, double* out) {
+  if (!ctx) return PHYLO_EINVAL;
+  if (!out) return fail(ctx, PHYLO_EINVAL, "out is NULL");
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  // matrices and post-order levels, then the log-likelihood alone
+  if (ctx->flags & PHYLO_FLAG_NO_GRAPH) {
+    rc = run_phases(ctx, 0, 1, nullptr);
+    if (!rc) rc = run_phases(ctx, kPhaseLogLOnly, kPhaseLogLOnly, nullptr);
+  } else {
+    if (ctx->graph_dirty || ctx->phase_dirty) {
+      invalidate_graph(ctx);
+      rc = upload_descriptors(ctx);
+      if (rc) return rc;
+      ctx->graph_dirty = ctx->phase_dirty = false;
+    }
+    rc = run_phases(ctx, 0, kPhaseLogLOnly, &ctx->fwd_exec);
+  }
+  if (rc) return rc;
+  ctx->forward_valid = true;
+  if (out != ctx->dev<double>(ctx->L.out))
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->dev<double>(ctx->L.out), 8,
+                                  cudaMemcpyDeviceToDevice, ctx->stream),
+             "copy log-likelihood");
+  return PHYLO_OK;
+}
+
+int phylo_backward_device(phylo_ctx* ctx, double* out) {
+  if (!ctx) return PHYLO_EINVAL;
+  if (!out) return fail(ctx, PHYLO_EINVAL, "out is NULL");
+  if (!ctx->forward_valid)
+    return fail(ctx, PHYLO_ESTATE, "backward needs a forward pass on the current inputs");
+  int rc;
+  if (ctx->flags & PHYLO_FLAG_NO_GRAPH) rc = run_phases(ctx, 2, 3, nullptr);
+  else rc = run_phases(ctx, 2, 3, &ctx->bwd_exec);
+  if (rc) return rc;
+  if (out != ctx->dev<double>(ctx->L.out) + 1)
+    CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->dev<double>(ctx->L.out) + 1,
+                                  (2 * (size_t)ctx->N - 2) * 8, cudaMemcpyDeviceToDevice,
+                                  ctx->stream),
+             "copy gradient");
   return PHYLO_OK;
 }
 
