@@ -942,6 +942,7 @@ inline size_t wide_pre_smem(int R) {
 }  // namespace phylo
 
 #include "kernels_p4.cuh"
+#include "kernels_tc64.cuh"
 
 namespace phylo {
 
@@ -1020,14 +1021,17 @@ cudaError_t launch_level_impl(const LevelArgs<T>& a, int SP, int RP, bool post,
       if constexpr (std::is_same<T, float>::value) return launch_p4_rp(a, RP, post, st);
       else return launch_small_rp<T, 4>(a, RP, post, st);
     case 20: return launch_small_rp<T, 20>(a, RP, post, st);
-    case 64: {
-      dim3 grid(a.n_tiles, a.n_level);
-      if (post)
-        post_wide_kernel<T><<<grid, kWideThreads, wide_post_smem<T>(), st>>>(a);
-      else
-        pre_wide_kernel<T><<<grid, kWideThreads, wide_pre_smem<T>(a.n_cat), st>>>(a);
-      return cudaGetLastError();
-    }
+    case 64:
+      if constexpr (std::is_same<T, float>::value) {
+        return launch_tc64(a, post, st);
+      } else {
+        dim3 grid(a.n_tiles, a.n_level);
+        if (post)
+          post_wide_kernel<T><<<grid, kWideThreads, wide_post_smem<T>(), st>>>(a);
+        else
+          pre_wide_kernel<T><<<grid, kWideThreads, wide_pre_smem<T>(a.n_cat), st>>>(a);
+        return cudaGetLastError();
+      }
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1037,13 +1041,17 @@ cudaError_t prepare_impl(int SP, int RP) {
   if (SP == 4) return prepare_small_rp<T, 4>(RP);
   if (SP == 20) return prepare_small_rp<T, 20>(RP);
   if (SP == 64) {
-    cudaError_t e = cudaFuncSetAttribute(
-        post_wide_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)wide_post_smem<T>());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(pre_wide_kernel<T>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)wide_pre_smem<T>(8));
+    if constexpr (std::is_same<T, float>::value) {
+      return prepare_tc64();
+    } else {
+      cudaError_t e = cudaFuncSetAttribute(
+          post_wide_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+          (int)wide_post_smem<T>());
+      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(pre_wide_kernel<T>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)wide_pre_smem<T>(8));
+    }
   }
   return cudaSuccess;
 }

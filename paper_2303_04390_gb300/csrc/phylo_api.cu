@@ -36,7 +36,7 @@ struct Layout {
   int SP = 0, RP = 0, n_tiles = 0;
   size_t elem = 0;
   Region children, post_nodes, pre_nodes, post_desc, pre_desc;
-  Region P, dP, post, pre, escale;
+  Region P, dP, post, pre, escale, pre_escale;
   Region tip_states, tip_partials, tip_has;
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
@@ -89,8 +89,11 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.post, part);
   ok &= add_region(L, L.pre, part);
   if (C > (1 << 30)) return "n_patterns too large";
-  if (!mul_ok(n_int, (size_t)round_up(C, 4) * sizeof(int), &tmp)) return "size overflow";
+  const int planes = escale_planes(L.SP, R, prec == PHYLO_FP64);
+  if (!mul_ok(n_int * planes, (size_t)round_up(C, 4) * sizeof(int), &tmp))
+    return "size overflow";
   ok &= add_region(L, L.escale, tmp);
+  if (uses_tensor_cores(L.SP, prec == PHYLO_FP64)) ok &= add_region(L, L.pre_escale, tmp);
   if (!mul_ok((size_t)N, (size_t)round_up(C, 16), &tmp)) return "size overflow";
   ok &= add_region(L, L.tip_states, tmp);
   if (!mul_ok((size_t)N, (size_t)C, &tmp)) return "size overflow";
@@ -208,6 +211,7 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.post = ctx->dev<T>(ctx->L.post);
   a.pre = ctx->dev<T>(ctx->L.pre);
   a.escale = ctx->dev<int>(ctx->L.escale);
+  a.pre_escale = ctx->L.pre_escale.bytes ? ctx->dev<int>(ctx->L.pre_escale) : nullptr;
   a.tip_states = ctx->dev<uint8_t>(ctx->L.tip_states);
   a.state_stride = round_up(ctx->C, 16);
   a.escale_stride = round_up(ctx->C, 4);

@@ -51,9 +51,21 @@ constexpr int kWidePatternsF64 = 8;
 #endif
 constexpr int kP4TilePatterns = PHYLO_P4_TILE;
 
+// FP32 with 21..64 states runs on the tensor cores (kernels_tc64.cuh):
+// 128-pattern tiles and one rescale exponent per (node, category, pattern).
+inline bool uses_tensor_cores(int SP, bool fp64) { return SP == 64 && !fp64; }
+constexpr int kTcTilePatterns = 128;
+
+// Exponent planes per node: R on the tensor-core path, else 1 (one
+// exponent per (node, pattern) shared by all categories).
+inline int escale_planes(int SP, int R, bool fp64) {
+  return uses_tensor_cores(SP, fp64) ? R : 1;
+}
+
 // Patterns of one tile (the unit of the per-tile gradient sums).
 inline int patterns_per_tile(int SP, int R, bool fp64) {
   if (SP == 4 && !fp64) return kP4TilePatterns;
+  if (uses_tensor_cores(SP, fp64)) return kTcTilePatterns;
   if (SP <= 20) return kSmallThreads / lanes_per_pattern(R);
   return fp64 ? kWidePatternsF64 : kWidePatternsF32;
 }
@@ -72,7 +84,10 @@ struct LevelArgs {
   const T* dP;                 // same layout: dP/dt = gamma_r Q P
   T* post;                     // [N-1][C][R][SP] post-order partials
   T* pre;                      // [N-1][C][R][SP] pre-order partials
-  int* escale;                 // [N-1][escale_stride] cumulative exponents
+  int* escale;                 // [N-1][planes][escale_stride] cumulative
+                               // post-order exponents (planes: escale_planes)
+  int* pre_escale;             // [N-1][R][escale_stride] cumulative pre-order
+                               // exponents (tensor-core path only, else null)
   const uint8_t* tip_states;   // [N][state_stride]; value S = gap
   int state_stride;            // C rounded up to 16 (16-byte rows)
   int escale_stride;           // C rounded up to 4 (16-byte rows)

@@ -56,7 +56,8 @@ struct NaRegion {
 
 struct NaLayout {
   int SP = 0, RP = 0, n_tiles = 0;
-  NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale;
+  NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale,
+      pre_escale;
   NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
   NaRegion gpart, lpart, out, pattern_wt, cat_wt, pi_t;
   size_t total = 0;
@@ -88,7 +89,9 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.dP, mat);
   na_add(L, L.post, part);
   na_add(L, L.pre, part);
-  na_add(L, L.escale, n_int * (size_t)round_up(C, 4) * sizeof(int));
+  const size_t eplane = n_int * (size_t)round_up(C, 4) * sizeof(int);
+  na_add(L, L.escale, eplane * escale_planes(L.SP, R, false));
+  if (uses_tensor_cores(L.SP, false)) na_add(L, L.pre_escale, eplane * R);
   na_add(L, L.tip_states, (size_t)N * round_up(C, 16));
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
@@ -336,6 +339,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   a.post = reinterpret_cast<float*>(ws + L.post.off);
   a.pre = reinterpret_cast<float*>(ws + L.pre.off);
   a.escale = reinterpret_cast<int*>(ws + L.escale.off);
+  a.pre_escale = L.pre_escale.bytes ? reinterpret_cast<int*>(ws + L.pre_escale.off) : nullptr;
   a.tip_states = reinterpret_cast<const uint8_t*>(ws + L.tip_states.off);
   a.state_stride = round_up(C, 16);
   a.escale_stride = round_up(C, 4);

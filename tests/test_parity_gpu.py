@@ -58,6 +58,10 @@ SMALL = [
     (6, 33, 2, 20, "balanced"),
     (5, 64, 1, 17, "yule"),
     (24, 61, 4, 37, "caterpillar"),
+    (14, 61, 4, 300, "yule"),          # several 128-pattern tiles, ragged tail
+    (6, 45, 3, 129, "caterpillar"),    # a tail of one pattern
+    (40, 61, 4, 1, "yule"),
+    (120, 61, 4, 130, "caterpillar"),  # deep chain: rescaling at every node
 ]
 
 
@@ -89,8 +93,9 @@ def test_tip_partials(S, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_zero_length_branches(precision):
-    w = synth.small_workload(15, 4, 4, 80, seed=23)
+@pytest.mark.parametrize("S", [4, 61])
+def test_zero_length_branches(S, precision):
+    w = synth.small_workload(15, S, 4, 80, seed=23)
     t = w.t.copy()
     root = 2 * w.n_tips - 2
     a = int(np.nonzero(w.parent == root)[0][0])
