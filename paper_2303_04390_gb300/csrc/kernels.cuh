@@ -185,7 +185,7 @@ template <> struct Acc<float> {
   using type = F2;
   __device__ static F2 zero() { return {0.f, 0.f}; }
   __device__ static F2 prod(float w, float g) {
-    const float p = w * g;
+    const float p = __fmul_rn(w, g);  // never fused into a later add
     return {p, fmaf(w, g, -p)};
   }
   __device__ static F2 add(F2 a, F2 b) { return f2_add(a, b); }
@@ -1067,10 +1067,21 @@ cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
       break;
     }
     case 20: pmat_kernel<T, 20><<<units, 256, 0, st>>>(a); break;
-    case 64: pmat_kernel<T, 64><<<units, 256, 0, st>>>(a); break;
+    case 64:
+      if constexpr (std::is_same<T, float>::value) return launch_pmat_tc64(a, st);
+      else pmat_kernel<T, 64><<<units, 256, 0, st>>>(a);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pre_finish_impl(const LevelArgs<T>& a, int SP, cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (SP == 64) return launch_ratio_tc64(a, st);
+  }
+  return cudaSuccess;
 }
 
 }  // namespace phylo
@@ -1090,6 +1101,11 @@ cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
   cudaError_t launch_pre_level<T>(const LevelArgs<T>& a, int SP, int RP,      \
                                   cudaStream_t st) {                          \
     return launch_level_impl<T>(a, SP, RP, false, st);                        \
+  }                                                                           \
+  template <>                                                                 \
+  cudaError_t launch_pre_finish<T>(const LevelArgs<T>& a, int SP,             \
+                                   cudaStream_t st) {                         \
+    return launch_pre_finish_impl<T>(a, SP, st);                              \
   }                                                                           \
   template <>                                                                 \
   cudaError_t prepare_kernels<T>(int SP, int RP) {                            \

@@ -36,7 +36,7 @@ struct Layout {
   int SP = 0, RP = 0, n_tiles = 0;
   size_t elem = 0;
   Region children, post_nodes, pre_nodes, post_desc, pre_desc;
-  Region P, dP, post, pre, escale, pre_escale;
+  Region P, dP, post, pre, escale, pre_escale, rterm;
   Region tip_states, tip_partials, tip_has;
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
@@ -75,7 +75,9 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   const size_t n_nodes = 2 * (size_t)N - 1, n_br = 2 * (size_t)N - 2;
   const size_t n_int = (size_t)N - 1;
   size_t mat, part, tmp, tmp2;
-  if (!mul_ok(n_br * R, (size_t)L.SP * L.SP * L.elem, &mat)) return "size overflow";
+  const bool tc = uses_tensor_cores(L.SP, prec == PHYLO_FP64);
+  if (!mul_ok(n_br * R, tc ? kTcUnitBytes : (size_t)L.SP * L.SP * L.elem, &mat))
+    return "size overflow";
   if (!mul_ok(n_int, (size_t)C, &tmp) || !mul_ok(tmp, (size_t)R * L.SP * L.elem, &part))
     return "size overflow";
   bool ok = true;
@@ -85,7 +87,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.post_desc, n_int * sizeof(int4));
   ok &= add_region(L, L.pre_desc, n_int * sizeof(int4));
   ok &= add_region(L, L.P, mat);
-  ok &= add_region(L, L.dP, mat);
+  ok &= add_region(L, L.dP, tc ? 0 : mat);  // the tensor-core tiles hold dP
   ok &= add_region(L, L.post, part);
   ok &= add_region(L, L.pre, part);
   if (C > (1 << 30)) return "n_patterns too large";
@@ -93,7 +95,11 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   if (!mul_ok(n_int * planes, (size_t)round_up(C, 4) * sizeof(int), &tmp))
     return "size overflow";
   ok &= add_region(L, L.escale, tmp);
-  if (uses_tensor_cores(L.SP, prec == PHYLO_FP64)) ok &= add_region(L, L.pre_escale, tmp);
+  if (tc) {
+    ok &= add_region(L, L.pre_escale, tmp);
+    if (!mul_ok(n_int * C, (size_t)R * 16, &tmp)) return "size overflow";
+    ok &= add_region(L, L.rterm, tmp);
+  }
   if (!mul_ok((size_t)N, (size_t)round_up(C, 16), &tmp)) return "size overflow";
   ok &= add_region(L, L.tip_states, tmp);
   if (!mul_ok((size_t)N, (size_t)C, &tmp)) return "size overflow";
@@ -207,11 +213,12 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.n_cat = ctx->R;
   a.root = 2 * ctx->N - 2;
   a.P = ctx->dev<T>(ctx->L.P);
-  a.dP = ctx->dev<T>(ctx->L.dP);
+  a.dP = ctx->L.dP.bytes ? ctx->dev<T>(ctx->L.dP) : nullptr;
   a.post = ctx->dev<T>(ctx->L.post);
   a.pre = ctx->dev<T>(ctx->L.pre);
   a.escale = ctx->dev<int>(ctx->L.escale);
   a.pre_escale = ctx->L.pre_escale.bytes ? ctx->dev<int>(ctx->L.pre_escale) : nullptr;
+  a.rterm = ctx->L.rterm.bytes ? ctx->dev<void>(ctx->L.rterm) : nullptr;
   a.tip_states = ctx->dev<uint8_t>(ctx->L.tip_states);
   a.state_stride = round_up(ctx->C, 16);
   a.escale_stride = round_up(ctx->C, 4);
@@ -273,10 +280,12 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
       a.level_nodes = nodes + off[l];
       a.level_desc = desc + off[l];
       a.n_level = off[l + 1] - off[l];
+      a.root_level = post && l + 2 == off.size();  // the last post level is the root
       e = post ? launch_post_level<T>(a, ctx->L.SP, ctx->L.RP, st)
                : launch_pre_level<T>(a, ctx->L.SP, ctx->L.RP, st);
       if (e != cudaSuccess) return e;
     }
+    if (!post && ctx->C > 0) return launch_pre_finish<T>(a, ctx->L.SP, st);
     return cudaSuccess;
   }
   ReduceArgs ra{};
@@ -1014,8 +1023,10 @@ int phylo_check(phylo_ctx* ctx) {
 int phylo_launches_per_evaluation(const phylo_ctx* ctx) {
   if (!ctx || !ctx->have_tree) return 0;
   int n = 2;  // pmat + final reduction
-  if (ctx->C > 0)
+  if (ctx->C > 0) {
     n += (int)(ctx->post_off.size() - 1) + (int)(ctx->pre_off.size() - 1);
+    if (uses_tensor_cores(ctx->L.SP, ctx->precision == PHYLO_FP64)) ++n;  // Eq. 8 ratios
+  }
   return n;
 }
 

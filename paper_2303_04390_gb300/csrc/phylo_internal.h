@@ -55,6 +55,9 @@ constexpr int kP4TilePatterns = PHYLO_P4_TILE;
 // 128-pattern tiles and one rescale exponent per (node, category, pattern).
 inline bool uses_tensor_cores(int SP, bool fp64) { return SP == 64 && !fp64; }
 constexpr int kTcTilePatterns = 128;
+// Matrix operand tiles of one (branch, category) on that path: [P; dP] and
+// P' as split TF32 pairs (kernels_tc64.cuh gives the layout).
+constexpr size_t kTcUnitBytes = 98304;
 
 // Exponent planes per node: R on the tensor-core path, else 1 (one
 // exponent per (node, pattern) shared by all categories).
@@ -79,9 +82,12 @@ struct LevelArgs {
   const int* level_nodes;      // internal nodes of this level
   const int4* level_desc;      // per level node: {k, child 0, child 1, flags}
   int n_level;                 // number of nodes in the level
+  int root_level;              // 1 if the level is the root alone
   int n_tips, n_patterns, n_states, n_cat, root;
   const T* P;                  // [2N-2][R][SP][SP], row = parent state
-  const T* dP;                 // same layout: dP/dt = gamma_r Q P
+                               // (tensor-core path: [2N-2][R] operand tiles)
+  const T* dP;                 // same layout: dP/dt = gamma_r Q P (null on
+                               // the tensor-core path, whose tiles hold dP)
   T* post;                     // [N-1][C][R][SP] post-order partials
   T* pre;                      // [N-1][C][R][SP] pre-order partials
   int* escale;                 // [N-1][planes][escale_stride] cumulative
@@ -99,6 +105,8 @@ struct LevelArgs {
   const T* pattern_wt;         // [C] the same weights in T
   const T* cat_wt;             // [R] the same weights in T
   const T* root_pit;           // [S] the root distribution in T
+  void* rterm;                 // tensor-core path: [N-1][C][R] float4 Eq. 8
+                               // terms of each category (else null)
   double* gpart;               // [2N-2][n_tiles] per-tile gradient sums
   double* lpart;               // [n_tiles] per-tile log-likelihood sums
   int n_tiles;
@@ -133,6 +141,10 @@ cudaError_t launch_post_level(const LevelArgs<T>& a, int SP, int RP,
 template <typename T>
 cudaError_t launch_pre_level(const LevelArgs<T>& a, int SP, int RP,
                              cudaStream_t st);
+// Work after the last pre-order level (the tensor-core path's Eq. 8
+// ratios); a no-op elsewhere.
+template <typename T>
+cudaError_t launch_pre_finish(const LevelArgs<T>& a, int SP, cudaStream_t st);
 template <typename T>
 cudaError_t prepare_kernels(int SP, int RP);
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);

@@ -57,7 +57,7 @@ struct NaRegion {
 struct NaLayout {
   int SP = 0, RP = 0, n_tiles = 0;
   NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale,
-      pre_escale;
+      pre_escale, rterm;
   NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
   NaRegion gpart, lpart, out, pattern_wt, cat_wt, pi_t;
   size_t total = 0;
@@ -78,7 +78,8 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   const int ct = patterns_per_tile(L.SP, R, false);
   L.n_tiles = (C + ct - 1) / ct;
   const size_t n_nodes = 2 * (size_t)N - 1, n_br = 2 * (size_t)N - 2, n_int = (size_t)N - 1;
-  const size_t mat = n_br * R * L.SP * L.SP * sizeof(float);
+  const bool tc = uses_tensor_cores(L.SP, false);
+  const size_t mat = n_br * R * (tc ? kTcUnitBytes : L.SP * L.SP * sizeof(float));
   const size_t part = n_int * (size_t)C * R * L.SP * sizeof(float);
   na_add(L, L.children, n_nodes * sizeof(int2));
   na_add(L, L.post_nodes, n_int * sizeof(int));
@@ -86,12 +87,15 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.post_desc, n_int * sizeof(int4));
   na_add(L, L.pre_desc, n_int * sizeof(int4));
   na_add(L, L.P, mat);
-  na_add(L, L.dP, mat);
+  na_add(L, L.dP, tc ? 0 : mat);  // the tensor-core tiles hold dP
   na_add(L, L.post, part);
   na_add(L, L.pre, part);
   const size_t eplane = n_int * (size_t)round_up(C, 4) * sizeof(int);
   na_add(L, L.escale, eplane * escale_planes(L.SP, R, false));
-  if (uses_tensor_cores(L.SP, false)) na_add(L, L.pre_escale, eplane * R);
+  if (tc) {
+    na_add(L, L.pre_escale, eplane * R);
+    na_add(L, L.rterm, n_int * (size_t)C * R * 16);
+  }
   na_add(L, L.tip_states, (size_t)N * round_up(C, 16));
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
@@ -335,11 +339,12 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   a.n_cat = R;
   a.root = root;
   a.P = reinterpret_cast<const float*>(ws + L.P.off);
-  a.dP = reinterpret_cast<const float*>(ws + L.dP.off);
+  a.dP = L.dP.bytes ? reinterpret_cast<const float*>(ws + L.dP.off) : nullptr;
   a.post = reinterpret_cast<float*>(ws + L.post.off);
   a.pre = reinterpret_cast<float*>(ws + L.pre.off);
   a.escale = reinterpret_cast<int*>(ws + L.escale.off);
   a.pre_escale = L.pre_escale.bytes ? reinterpret_cast<int*>(ws + L.pre_escale.off) : nullptr;
+  a.rterm = L.rterm.bytes ? static_cast<void*>(ws + L.rterm.off) : nullptr;
   a.tip_states = reinterpret_cast<const uint8_t*>(ws + L.tip_states.off);
   a.state_stride = round_up(C, 16);
   a.escale_stride = round_up(C, 4);
@@ -363,14 +368,17 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
     a.level_nodes = dpost + post_off[l];
     a.level_desc = dpostd + post_off[l];
     a.n_level = post_off[l + 1] - post_off[l];
+    a.root_level = l + 1 == n_post;  // the last post level is the root alone
     NA_TRY(launch_post_level<float>(a, L.SP, L.RP, st), "post-order level");
   }
+  a.root_level = 0;
   for (int l = 0; l < n_pre; ++l) {
     a.level_nodes = dpre + pre_off[l];
     a.level_desc = dpred + pre_off[l];
     a.n_level = pre_off[l + 1] - pre_off[l];
     NA_TRY(launch_pre_level<float>(a, L.SP, L.RP, st), "pre-order level");
   }
+  if (C > 0) NA_TRY(launch_pre_finish<float>(a, L.SP, st), "gradient ratios");
   ReduceArgs ra{};
   ra.gpart = a.gpart;
   ra.lpart = a.lpart;
