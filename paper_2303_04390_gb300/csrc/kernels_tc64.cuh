@@ -9,17 +9,19 @@
 //          num_x = a_x . V_x,  den = a_i . U_i      (per pattern)
 //          q_i = a_i P_i,  q_j = a_j P_j             (internal children)
 // Every product with a partial tile is a 128 x N x 64 contraction issued as
-// tcgen05.mma kind::tf32 with FP32 accumulation in TMEM.  FP32 accuracy
-// comes from splitting both operands into TF32 hi and remainder lo and
-// summing Ahi Bhi + Ahi Blo + Alo Bhi (three passes).  After each
-// contraction one thread per pattern reads its accumulator row back from
-// TMEM, so products, dot products and the rescale are thread-local.
+// tcgen05.mma kind::f16 on BF16 operands with FP32 accumulation in TMEM.
+// FP32 accuracy comes from splitting each operand into three BF16 terms
+// and summing the six products of order up to 2^-16 (tc.cuh); BF16 MMAs
+// run at eight times the TF32 rate on this GPU, so the six cost less
+// tensor time than a three-pass TF32 split.  After each contraction one
+// thread per pattern reads its accumulator row back from TMEM, so
+// products, dot products and the rescale are thread-local.
 //
 // Matrices.  The transition-matrix kernel of this path writes, per (branch,
 // r), the operand tiles the level kernels consume, already split and in the
 // K-major 128-byte-swizzle layout of tc.cuh, so a level kernel stages them
 // with 1-D bulk copies (cp.async.bulk) that overlap its partial loads:
-//   [PdP hi | PdP lo | Pt hi | Pt lo]
+//   [PdP term 0 | term 1 | term 2 | Pt term 0 | term 1 | term 2]
 //   PdP: 128-row tile, rows 0..63 = rows of P, rows 64..127 = rows of dP
 //   Pt:  64-row tile, row t = column t of P
 // A compact tip reads its column of P or dP out of the staged tiles.
@@ -47,21 +49,26 @@
 namespace phylo {
 
 constexpr int kTcRows = kTcTilePatterns;  // patterns per tile (MMA M)
-constexpr int kTcThreads = 128;           // one thread per pattern row
-static_assert(kTcRows == kTcThreads, "one thread per accumulator lane");
+// Level kernels: two threads per pattern row, thread t owning row t % 128
+// and columns [32h, 32h + 32) with h = t / 128.  Warp w reads TMEM lanes
+// 32 (w % 4) .. 32 (w % 4) + 31, which are exactly its rows.
+constexpr int kTcThreads = 2 * kTcRows;
+static_assert(kTcRows == 128, "one accumulator lane per pattern row");
 
-constexpr uint32_t kTile128 = 128 * 256;  // 128 rows x 64 FP32
-constexpr uint32_t kTile64 = 64 * 256;
+constexpr uint32_t kTerm128 = 128 * 128;  // one BF16 term of a 128 x 64 tile
+constexpr uint32_t kTerm64 = 64 * 128;    // one BF16 term of a 64 x 64 tile
+constexpr uint32_t kOp128 = 3 * kTerm128;  // three-term 128-row operand
+constexpr uint32_t kOp64 = 3 * kTerm64;    // three-term 64-row operand
 // Matrix tiles of one (branch, r) in the workspace.
-constexpr uint32_t kUnitPdpHi = 0, kUnitPdpLo = kTile128;
-constexpr uint32_t kUnitPtHi = 2 * kTile128, kUnitPtLo = 2 * kTile128 + kTile64;
-static_assert(kTcUnitBytes == 2 * kTile128 + 2 * kTile64, "matrix tile block size");
+constexpr uint32_t kUnitPdp = 0, kUnitPt = kOp128;
+static_assert(kTcUnitBytes == kOp128 + kOp64, "matrix tile block size");
 
 // Dynamic shared memory (+1024 for the alignment of the swizzled tiles):
-//   post: A_i, A_j (hi+lo, 64 KB each) | B_i, B_j (P hi+lo, 32 KB each)
-//   pre:  A (64 KB; later Pt_i, Pt_j) | PdP_i, PdP_j (hi+lo, 64 KB each)
-constexpr size_t kTcPostSmem = 1024 + 4 * kTile128 + 4 * kTile64;
-constexpr size_t kTcPreSmem = 1024 + 2 * kTile128 + 4 * kTile128;
+//   post: A_i, A_j (48 KB each) | B_i, B_j (P, 24 KB each)
+//   pre:  A_i, A_j (48 KB each; later Pt_i, Pt_j) | PdP_i, PdP_j (48 KB
+//         each; later a_i, a_j as A operands)
+constexpr size_t kTcPostSmem = 1024 + 2 * kOp128 + 2 * kOp64;
+constexpr size_t kTcPreSmem = 1024 + 4 * kOp128;
 
 __device__ __forceinline__ float pow2i(int d) {  // 2^d for d <= 0 (0 below 2^-126)
   return d < -126 ? 0.f : __uint_as_float((unsigned)(127 + d) << 23);
@@ -87,20 +94,93 @@ __device__ __forceinline__ bool tc_block_wait(uint64_t* bar, uint32_t& parity, i
   return ok;
 }
 
-// Load this thread's row of a partial tile (64 FP32) into registers.
-__device__ __forceinline__ void load_row(float4 (&v)[16], const float* __restrict__ src,
-                                         bool valid) {
-#pragma unroll
-  for (int j = 0; j < 16; ++j)
-    v[j] = valid ? __ldg(reinterpret_cast<const float4*>(src) + j)
-                 : make_float4(0.f, 0.f, 0.f, 0.f);
+// Cooperative, coalesced access to a 128-row tile of 64-float rows (row
+// c0 + m at base + (c0 + m) * stride): in iteration it (0..3) lane l of
+// warp w handles row 32 it + 4 w + l / 8 and floats 8 (l % 8) .. + 7, so a
+// warp instruction touches 4 rows in full rather than 32 rows in part.
+__device__ __forceinline__ int coop_row(int it) {
+  return 32 * it + 4 * (int)(threadIdx.x >> 5) + (int)((threadIdx.x & 31) >> 3);
 }
 
-// Split a register row into the hi/lo A tiles (row `row`).
-__device__ __forceinline__ void put_row(unsigned char* hi, unsigned char* lo, int row,
-                                        const float4 (&v)[16]) {
+__device__ __forceinline__ void coop_load(float4 (&v)[8], const float* __restrict__ base,
+                                          size_t stride, int c0, int C) {
+  const int j = threadIdx.x & 7;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) tc::put_split4(hi, lo, row, j, kTcRows, v[j]);
+  for (int it = 0; it < 4; ++it) {
+    const int c = c0 + coop_row(it);
+    if (c < C) {
+      const float4* src = reinterpret_cast<const float4*>(base + (size_t)c * stride + 8 * j);
+      v[2 * it] = __ldg(src);
+      v[2 * it + 1] = __ldg(src + 1);
+    } else {
+      v[2 * it] = v[2 * it + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// Split a cooperatively loaded tile into the three BF16 term tiles of a
+// 128-row operand at `op`.
+__device__ __forceinline__ void coop_put(unsigned char* op, const float4 (&v)[8]) {
+  const int j = threadIdx.x & 7;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const float x[8] = {v[2 * it].x, v[2 * it].y, v[2 * it].z, v[2 * it].w,
+                        v[2 * it + 1].x, v[2 * it + 1].y, v[2 * it + 1].z, v[2 * it + 1].w};
+    tc::put_split3(op, op + kTerm128, op + 2 * kTerm128, coop_row(it), j, x);
+  }
+}
+
+// Row staging in shared memory for coalesced transfers: [128][kStageLd]
+// floats (the 4-float pad keeps both access patterns free of bank
+// conflicts).
+constexpr int kStageLd = 68;
+constexpr uint32_t kStageBytes = kTcRows * kStageLd * 4;
+
+// Thread (row, h) writes its half row (32 values times f) to the staging.
+__device__ __forceinline__ void stage_half(float* st, int row, int h, const float (&p)[32],
+                                           float f) {
+#pragma unroll
+  for (int i = 0; i < 32; i += 4)
+    *reinterpret_cast<float4*>(st + row * kStageLd + 32 * h + i) =
+        make_float4(p[i] * f, p[i + 1] * f, p[i + 2] * f, p[i + 3] * f);
+}
+
+// Coalesced store of the staged rows: a quarter warp writes one 128-byte
+// half row per instruction.
+__device__ __forceinline__ void coop_store(float* __restrict__ base, size_t stride, int c0,
+                                           int C, const float* st) {
+  const int jj = threadIdx.x & 7;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int row = coop_row(it), c = c0 + row;
+    if (c < C) {
+      float* dst = base + (size_t)c * stride;
+      *reinterpret_cast<float4*>(dst + 4 * jj) =
+          *reinterpret_cast<const float4*>(st + row * kStageLd + 4 * jj);
+      *reinterpret_cast<float4*>(dst + 32 + 4 * jj) =
+          *reinterpret_cast<const float4*>(st + row * kStageLd + 32 + 4 * jj);
+    }
+  }
+}
+
+// Write a cooperatively loaded tile into the staging (raw FP32).
+__device__ __forceinline__ void coop_stage(float* st, const float4 (&v)[8]) {
+  const int j = threadIdx.x & 7;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    float* d = st + coop_row(it) * kStageLd + 8 * j;
+    *reinterpret_cast<float4*>(d) = v[2 * it];
+    *reinterpret_cast<float4*>(d + 4) = v[2 * it + 1];
+  }
+}
+
+// Shared addresses of the three terms of an operand.
+__device__ __forceinline__ void term_addrs(const unsigned char* op, uint32_t term,
+                                           uint32_t (&t)[3]) {
+  const uint32_t a = smem_addr(op);
+  t[0] = a;
+  t[1] = a + term;
+  t[2] = a + 2 * term;
 }
 
 struct TcChild {
@@ -113,12 +193,17 @@ __device__ __forceinline__ TcChild tc_child(int n_tips, int b, bool compact) {
   return TcChild{b, compact, b >= n_tips};
 }
 
-__device__ __forceinline__ const float* child_row(const LevelArgs<float>& a, const TcChild& x,
-                                                  int c, int r) {
+// First row (pattern 0, category r) of a non-compact child's partials and
+// the row stride, in floats.
+__device__ __forceinline__ const float* child_base(const LevelArgs<float>& a, const TcChild& x,
+                                                   int r, size_t* stride) {
   const int C = a.n_patterns;
-  if (x.internal)
-    return a.post + (((size_t)(x.b - a.n_tips) * C + c) * a.n_cat + r) * 64;
-  return a.tip_partials + ((size_t)x.b * C + c) * 64;
+  if (x.internal) {
+    *stride = (size_t)a.n_cat * 64;
+    return a.post + ((size_t)(x.b - a.n_tips) * C * a.n_cat + r) * 64;
+  }
+  *stride = 64;
+  return a.tip_partials + (size_t)x.b * C * 64;
 }
 
 __device__ __forceinline__ const unsigned char* unit_tiles(const LevelArgs<float>& a, int b,
@@ -127,20 +212,22 @@ __device__ __forceinline__ const unsigned char* unit_tiles(const LevelArgs<float
          ((size_t)b * a.n_cat + r) * kTcUnitBytes;
 }
 
-// 16 accumulator columns of this thread's row, or for a compact tip the
-// matching entries of its matrix column (rows row0 + s of a staged tile
-// with `rows` rows; a gap selects the all-ones vector).
-__device__ __forceinline__ void child_chunk(const TcChild& x, int y, int S, uint32_t taddr,
-                                            const unsigned char* hi, const unsigned char* lo,
-                                            int rows, int row0, int s0, float (&u)[16]) {
+// 32 accumulator columns of this thread's row, or for a compact tip the
+// matching entries (states s0..s0+31) of its matrix column (rows row0 + s
+// of a staged three-term operand with term stride `term`; a gap selects
+// the all-ones vector).
+__device__ __forceinline__ void child_cols(const TcChild& x, int y, int S, uint32_t taddr,
+                                           const unsigned char* op, uint32_t term, int row0,
+                                           int s0, float (&u)[32]) {
   if (!x.compact) {
-    tc::ld16(taddr, u);
+    tc::ld32(taddr, u);
     return;
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < 32; ++i) {
     const int s = s0 + i;
-    u[i] = y < S ? tc::get_split(hi, lo, row0 + s, y, rows) : (s < S ? 1.f : 0.f);
+    u[i] = y < S ? tc::get_split3(op, op + term, op + 2 * term, row0 + s, y)
+                 : (s < S ? 1.f : 0.f);
   }
 }
 
@@ -154,7 +241,8 @@ __device__ __forceinline__ void child_chunk(const TcChild& x, int y, int S, uint
 // split exactly with fmaf, sums with Knuth's TwoSum), about 48 significant
 // bits, which keeps the small off-diagonal entries of short branches
 // accurate to FP32 despite the cancellation in the sum over eigenvalues.
-// The results are rounded to FP32 and written as the split operand tiles.
+// The results are rounded once to FP32 and written as the split operand
+// tiles.  V and Vinv arrive as double-float tables built on the host.
 struct DF {
   float h, l;
 };
@@ -183,12 +271,44 @@ __device__ __forceinline__ void df_fma(DF& acc, DF a, DF b) {
   acc.l = __fadd_rn(acc.l, __fadd_rn(e, p.l));
 }
 
+// FP32 value of acc (+ 1 when `one`), rounded once.
+__device__ __forceinline__ float df_round(DF acc, bool one) {
+  if (!one) return __fadd_rn(acc.h, acc.l);
+  const float s = __fadd_rn(acc.h, 1.f);
+  const float bb = __fsub_rn(s, acc.h);
+  const float e = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(1.f, bb));
+  return __fadd_rn(s, __fadd_rn(e, acc.l));
+}
+
+// Store 4 consecutive elements (k = k0..k0+3, k0 % 4 == 0) of row `row` of
+// a three-term BF16 operand at `op` with term stride `term`.
+__device__ __forceinline__ void put_split3_4(unsigned char* op, uint32_t term, int row, int k0,
+                                             float4 v) {
+  float x[4] = {v.x, v.y, v.z, v.w};
+  const uint32_t off = tc::b16_off(row, k0);
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(x[0], x[1]);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(x[2], x[3]);
+    const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+    x[0] = __fsub_rn(x[0], f0.x);
+    x[1] = __fsub_rn(x[1], f0.y);
+    x[2] = __fsub_rn(x[2], f1.x);
+    x[3] = __fsub_rn(x[3], f1.y);
+    *reinterpret_cast<uint2*>(op + t * term + off) =
+        make_uint2(*reinterpret_cast<const uint32_t*>(&h0), *reinterpret_cast<const uint32_t*>(&h1));
+  }
+}
+
 constexpr int kPmatTcThreads = 256;  // one 4 x 4 block of (s, t) per thread
 struct PmatTcSmem {
   float vt_h[64][64], vt_l[64][64];  // V transposed: [m][s]
   float vi_h[64][64], vi_l[64][64];  // Vinv: [m][t]
   DF e[64], d[64];
+  uint64_t bar;
 };
+static_assert(sizeof(float) * kEigenSplitFloats == 4 * 64 * 64 * sizeof(float),
+              "eigen table size");
 constexpr size_t kPmatTcSmem = sizeof(PmatTcSmem);
 
 template <typename T>  // float only
@@ -199,15 +319,10 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
   const int S = a.n_states, R = a.n_cat;
   const int unit = blockIdx.x, b = unit / R, r = unit % R;
   const int tid = threadIdx.x;
-  for (int i = tid; i < 64 * 64; i += kPmatTcThreads) {
-    const int m = i / 64, s = i % 64;
-    const bool in = m < S && s < S;
-    const DF v = df_from(in ? a.V[s * S + m] : 0.0);
-    const DF w = df_from(in ? a.Vinv[m * S + s] : 0.0);
-    sm.vt_h[m][s] = v.h;
-    sm.vt_l[m][s] = v.l;
-    sm.vi_h[m][s] = w.h;
-    sm.vi_l[m][s] = w.l;
+  if (tid == 0) {
+    mbar_init_fenced(&sm.bar, 1);
+    mbar_expect_tx(&sm.bar, (uint32_t)(kEigenSplitFloats * sizeof(float)));
+    bulk_g2s(&sm.vt_h[0][0], a.vsplit, (uint32_t)(kEigenSplitFloats * sizeof(float)), &sm.bar);
   }
   if (tid < 64) {
     double e = 0.0, de = 0.0;
@@ -225,7 +340,15 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
     sm.e[tid] = df_from(e);
     sm.d[tid] = df_from(de);
   }
-  __syncthreads();
+  __syncthreads();  // barrier initialised, exponentials staged
+  const bool ok = __syncthreads_and(mbar_wait(&sm.bar, 0));
+  if (!ok) {  // bounded drain, then give up on this unit
+    if (tid == 0) {
+      atomicOr(a.err, ERR_TIMEOUT);
+      (void)mbar_wait(&sm.bar, 0);
+    }
+    return;
+  }
   const int s0 = 4 * (tid / 16), t0 = 4 * (tid % 16);
   DF accP[4][4], accD[4][4];
 #pragma unroll
@@ -250,7 +373,6 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
       }
     }
   }
-  // Round to FP32 (adding the identity in FP64) and write the split tiles.
   unsigned char* base = static_cast<unsigned char*>(a.P) + (size_t)unit * kTcUnitBytes;
   float P[4][4], D[4][4];
 #pragma unroll
@@ -258,24 +380,20 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int s = s0 + i, t = t0 + j;
-      const double one = (s == t && s < S) ? 1.0 : 0.0;
-      P[i][j] = (float)(((double)accP[i][j].h + (double)accP[i][j].l) + one);
-      D[i][j] = (float)((double)accD[i][j].h + (double)accD[i][j].l);
+      P[i][j] = df_round(accP[i][j], s == t && s < S);
+      D[i][j] = df_round(accD[i][j], false);
     }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int s = s0 + i;
-    tc::put_split4(base + kUnitPdpHi, base + kUnitPdpLo, s, t0 / 4, 128,
-                   make_float4(P[i][0], P[i][1], P[i][2], P[i][3]));
-    tc::put_split4(base + kUnitPdpHi, base + kUnitPdpLo, 64 + s, t0 / 4, 128,
-                   make_float4(D[i][0], D[i][1], D[i][2], D[i][3]));
+    put_split3_4(base + kUnitPdp, kTerm128, s0 + i, t0,
+                 make_float4(P[i][0], P[i][1], P[i][2], P[i][3]));
+    put_split3_4(base + kUnitPdp, kTerm128, 64 + s0 + i, t0,
+                 make_float4(D[i][0], D[i][1], D[i][2], D[i][3]));
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int t = t0 + j;
-    tc::put_split4(base + kUnitPtHi, base + kUnitPtLo, t, s0 / 4, 64,
-                   make_float4(P[0][j], P[1][j], P[2][j], P[3][j]));
-  }
+  for (int j = 0; j < 4; ++j)
+    put_split3_4(base + kUnitPt, kTerm64, t0 + j, s0,
+                 make_float4(P[0][j], P[1][j], P[2][j], P[3][j]));
 }
 
 // ---------------------------------------------------------------------------
@@ -284,23 +402,25 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
 template <typename T>  // float only
 __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
+  static_assert(kStageBytes <= kOp128, "staging fits in an operand buffer");
   extern __shared__ unsigned char smraw[];
   unsigned char* base = align1024(smraw);
-  unsigned char* A_hi[2] = {base, base + 2 * kTile128};
-  unsigned char* A_lo[2] = {base + kTile128, base + 3 * kTile128};
-  unsigned char* B_hi[2] = {base + 4 * kTile128, base + 4 * kTile128 + 2 * kTile64};
-  unsigned char* B_lo[2] = {B_hi[0] + kTile64, B_hi[1] + kTile64};
+  unsigned char* A[2] = {base, base + kOp128};
+  unsigned char* B[2] = {base + 2 * kOp128, base + 2 * kOp128 + kOp64};
+  float* stage = reinterpret_cast<float*>(A[0]);  // output rows, after the MMAs
   __shared__ uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_slot;
-  __shared__ double lred[kTcThreads / 32];
+  __shared__ float xch[2][kTcRows];  // the two halves' partial row results
+  __shared__ double lred[kTcRows / 32];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & (kTcRows - 1), h = tid / kTcRows;
   const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
   const int4 d = a.level_desc[blockIdx.y];
   const int k = d.x;
   const TcChild xs[2] = {tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0),
                          tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1)};
   const bool any_mma = !xs[0].compact || !xs[1].compact;
-  const int c0 = blockIdx.x * kTcRows, c = c0 + tid;
+  const int c0 = blockIdx.x * kTcRows, c = c0 + row;
   const bool valid = c < C;
   const int estr = a.escale_stride;
   const bool root = k == a.root;
@@ -316,7 +436,7 @@ __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   uint32_t ptma = 0, pmma = 0;
   int pend_tma = -1, pend_mma = -1;
   bool ok = true;
@@ -325,48 +445,61 @@ __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
   int lexp = INT_MIN / 2;
   for (int r = r_begin; r < r_end && ok; ++r) {
     if (tid == 0) {
-      mbar_expect_tx(&bar_tma, 4 * kTile64);
+      mbar_expect_tx(&bar_tma, 2 * kOp64);
       for (int x = 0; x < 2; ++x) {
-        const unsigned char* src = unit_tiles(a, xs[x].b, r);
-        // rows 0..63 (P) of each K-atom of the 128-row PdP tile
-        bulk_g2s(B_hi[x], src + kUnitPdpHi, kTile64 / 2, &bar_tma);
-        bulk_g2s(B_hi[x] + kTile64 / 2, src + kUnitPdpHi + kTile128 / 2, kTile64 / 2, &bar_tma);
-        bulk_g2s(B_lo[x], src + kUnitPdpLo, kTile64 / 2, &bar_tma);
-        bulk_g2s(B_lo[x] + kTile64 / 2, src + kUnitPdpLo + kTile128 / 2, kTile64 / 2, &bar_tma);
+        const unsigned char* src = unit_tiles(a, xs[x].b, r) + kUnitPdp;
+        // rows 0..63 (P) of each term of the 128-row PdP operand
+        for (int t = 0; t < 3; ++t)
+          bulk_g2s(B[x] + t * kTerm64, src + t * kTerm128, kTerm64, &bar_tma);
       }
     }
-    for (int x = 0; x < 2; ++x) {
-      if (xs[x].compact) continue;
-      float4 v[16];
-      load_row(v, child_row(a, xs[x], valid ? c : c0, r), valid);
-      put_row(A_hi[x], A_lo[x], tid, v);
+    // every global load of this category is issued before any is used
+    int E = 0;
+    if (valid)
+      for (int x = 0; x < 2; ++x)
+        if (xs[x].internal) E += a.escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c];
+    {
+      float4 v[2][8];
+      for (int x = 0; x < 2; ++x)
+        if (!xs[x].compact) {
+          size_t stride;
+          const float* src = child_base(a, xs[x], r, &stride);
+          coop_load(v[x], src, stride, c0, C);
+        }
+      for (int x = 0; x < 2; ++x)
+        if (!xs[x].compact) coop_put(A[x], v[x]);
     }
     tc::fence_smem_for_async();
     if (!(ok = tc_block_wait(&bar_tma, ptma, pend_tma, a.err))) break;
     if (any_mma) {
       if (tid == 0) {
         for (int x = 0; x < 2; ++x)
-          if (!xs[x].compact)
-            tc::mma_split3<64>(tmem + 64 * x, smem_addr(A_hi[x]), smem_addr(A_lo[x]),
-                               smem_addr(B_hi[x]), smem_addr(B_lo[x]));
+          if (!xs[x].compact) {
+            uint32_t ta[3], tb[3];
+            term_addrs(A[x], kTerm128, ta);
+            term_addrs(B[x], kTerm64, tb);
+            tc::mma_split_bf16x3<64>(tmem + 64 * x, ta, tb);
+          }
         tc::commit(&bar_mma);
       }
       if (!(ok = tc_block_wait(&bar_mma, pmma, pend_mma, a.err))) break;
     }
-    // epilogue: p = U_i o U_j in registers, its max, then scale and store
-    float p[64];
+    // epilogue: p = U_i o U_j on this half row, the row max, scale, store
+    float p[32];
     float m = 0.f;
+    {
+      float uj[32];
+      child_cols(xs[0], y[0], S, trow + 0 + 32 * h, B[0], kTerm64, 0, 32 * h, p);
+      child_cols(xs[1], y[1], S, trow + 64 + 32 * h, B[1], kTerm64, 0, 32 * h, uj);
 #pragma unroll
-    for (int s0 = 0; s0 < 64; s0 += 16) {
-      float ui[16], uj[16];
-      child_chunk(xs[0], y[0], S, trow + 0 + s0, B_hi[0], B_lo[0], 64, 0, s0, ui);
-      child_chunk(xs[1], y[1], S, trow + 64 + s0, B_hi[1], B_lo[1], 64, 0, s0, uj);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        p[s0 + i] = ui[i] * uj[i];
-        m = fmaxf(m, fabsf(p[s0 + i]));
+      for (int i = 0; i < 32; ++i) {
+        p[i] *= uj[i];
+        m = fmaxf(m, fabsf(p[i]));
       }
     }
+    xch[h][row] = m;
+    __syncthreads();
+    m = fmaxf(m, xch[1 - h][row]);
     // An all-zero vector is legitimate for one category (its terms vanish
     // wherever it is used); the root flags a pattern whose categories all
     // vanish.
@@ -377,25 +510,22 @@ __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
       e = max(e, -126);  // 2^-e stays finite for a subnormal maximum
     }
     const float f = ldexpf(1.f, -e);
-    int E = e;
-    if (valid)
-      for (int x = 0; x < 2; ++x)
-        if (xs[x].internal)
-          E += a.escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c];
+    E += e;
     if (!root) {
-      if (valid) {
-        float* out = a.post + (((size_t)(k - a.n_tips) * C + c) * R + r) * 64;
-#pragma unroll
-        for (int i = 0; i < 64; i += 4)
-          *reinterpret_cast<float4*>(out + i) =
-              make_float4(p[i] * f, p[i + 1] * f, p[i + 2] * f, p[i + 3] * f);
-        a.escale[((size_t)(k - a.n_tips) * R + r) * estr + c] = E;
-      }
+      stage_half(stage, row, h, p, f);
+      if (valid && h == 0) a.escale[((size_t)(k - a.n_tips) * R + r) * estr + c] = E;
+      __syncthreads();
+      coop_store(a.post + ((size_t)(k - a.n_tips) * C * R + r) * 64, (size_t)R * 64, c0, C,
+                 stage);
     } else {
       float pi_dot = 0.f;
 #pragma unroll
-      for (int i = 0; i < 64; ++i)
-        if (i < S) pi_dot = fmaf(a.root_pit[i], p[i] * f, pi_dot);
+      for (int i = 0; i < 32; ++i)
+        if (32 * h + i < S) pi_dot = fmaf(a.root_pit[32 * h + i], p[i] * f, pi_dot);
+      __syncthreads();  // the max exchange above is read; reuse the buffer
+      xch[h][row] = pi_dot;
+      __syncthreads();
+      pi_dot = xch[0][row] + xch[1][row];
       if (valid && pi_dot != 0.f) {
         // L_c = sum_r w_r 2^E_r (pi' p_r): running sum relative to the largest E
         const float term = a.cat_wt[r] * pi_dot;
@@ -408,23 +538,23 @@ __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
       }
     }
     tc::fence_before();
-    __syncthreads();  // TMEM and shared tiles are reused by the next category
+    __syncthreads();  // TMEM, shared tiles and xch are reused next
     tc::fence_after();
   }
   if (ok && root) {
     double term = 0.0;
-    if (valid) {
+    if (valid && h == 0) {
       if (!(lsum > 0.f) || !isfinite(lsum)) atomicOr(a.err, ERR_ZERO_PARTIAL);
       term = (double)a.pattern_wt[c] *
              (log((double)lsum) + (double)lexp * 0.69314718055994530942);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(kFull, term, o);
-    if (lane == 0) lred[warp] = term;
+    if (lane == 0 && h == 0) lred[warp] = term;
     __syncthreads();
     if (tid == 0) {
       double l = 0.0;
-      for (int w = 0; w < kTcThreads / 32; ++w) l += lred[w];
+      for (int w = 0; w < kTcRows / 32; ++w) l += lred[w];
       a.lpart[blockIdx.x] = l;
     }
   }
@@ -443,25 +573,26 @@ __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
 template <typename T>  // float only
 __global__ void __launch_bounds__(kTcThreads) pre_tc_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
+  static_assert(kStageBytes + 0 <= kOp128 && 2 * kOp64 <= kOp128, "buffer reuse fits");
   extern __shared__ unsigned char smraw[];
   unsigned char* base = align1024(smraw);
-  // A: the children's p tiles in turn; then Pt_i (hi, lo) and Pt_j (hi, lo)
-  unsigned char* A_hi = base;
-  unsigned char* A_lo = base + kTile128;
-  unsigned char* T_hi[2] = {base, base + 2 * kTile64};
-  unsigned char* T_lo[2] = {base + kTile64, base + 3 * kTile64};
-  // PdP_x: [P_x; dP_x] operand tiles; later a_x as an A operand
-  unsigned char* C_hi[2] = {base + 2 * kTile128, base + 4 * kTile128};
-  unsigned char* C_lo[2] = {base + 3 * kTile128, base + 5 * kTile128};
+  // A_x: the children's p tiles; after the first contractions A_0 holds Pt_i
+  // and Pt_j and A_1 stages q_k; after the second, both stage the q_x rows
+  unsigned char* A[2] = {base, base + kOp128};
+  unsigned char* Tt[2] = {base, base + kOp64};
+  // Cm_x: [P_x; dP_x] operand tiles; later a_x as an A operand
+  unsigned char* Cm[2] = {base + 2 * kOp128, base + 3 * kOp128};
   __shared__ uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_slot;
+  __shared__ float xch[2][3][kTcRows];  // the two halves' partial row results
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kTcRows - 1), h = tid / kTcRows;
   const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
   const int4 d = a.level_desc[blockIdx.y];
   const int k = d.x;
   const TcChild xs[2] = {tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0),
                          tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1)};
-  const int c0 = blockIdx.x * kTcRows, c = c0 + tid;
+  const int c0 = blockIdx.x * kTcRows, c = c0 + row;
   const bool valid = c < C;
   const int estr = a.escale_stride;
   const bool root = k == a.root;
@@ -478,167 +609,178 @@ __global__ void __launch_bounds__(kTcThreads) pre_tc_kernel(LevelArgs<T> a) {
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   uint32_t ptma = 0, pmma = 0;
   int pend_tma = -1, pend_mma = -1;
   bool ok = true;
   if (tid == 0) {
-    mbar_expect_tx(&bar_tma, 4 * kTile128);
-    for (int x = 0; x < 2; ++x) {
-      const unsigned char* src = unit_tiles(a, xs[x].b, r);
-      bulk_g2s(C_hi[x], src + kUnitPdpHi, kTile128, &bar_tma);
-      bulk_g2s(C_lo[x], src + kUnitPdpLo, kTile128, &bar_tma);
-    }
+    mbar_expect_tx(&bar_tma, 2 * kOp128);
+    for (int x = 0; x < 2; ++x)
+      bulk_g2s(Cm[x], unit_tiles(a, xs[x].b, r) + kUnitPdp, kOp128, &bar_tma);
   }
-  // the non-compact children in order; the second one's row is prefetched
-  // into registers while the first one's contraction runs
-  int order[2] = {0, 1}, n_mma = 0;
-  for (int x = 0; x < 2; ++x)
-    if (!xs[x].compact) order[n_mma++] = x;
-  float4 v[16];
-  if (n_mma > 0) {
-    load_row(v, child_row(a, xs[order[0]], valid ? c : c0, r), valid);
-    put_row(A_hi, A_lo, tid, v);
+  // every global load is issued before any is used
+  int E = 0, eq_k = 0, ep[2] = {0, 0};
+  if (valid) {
+    if (!root) eq_k = a.pre_escale[(kslot * R + r) * estr + c];
+    for (int x = 0; x < 2; ++x)
+      if (xs[x].internal) ep[x] = a.escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c];
+    E = eq_k + ep[0] + ep[1];
   }
-  if (n_mma > 1) load_row(v, child_row(a, xs[order[1]], valid ? c : c0, r), valid);
+  float4 qv[8];
+  if (!root) coop_load(qv, a.pre + (kslot * C * R + r) * 64, (size_t)R * 64, c0, C);
+  {
+    float4 v[2][8];
+    for (int x = 0; x < 2; ++x)
+      if (!xs[x].compact) {
+        size_t stride;
+        const float* src = child_base(a, xs[x], r, &stride);
+        coop_load(v[x], src, stride, c0, C);
+      }
+    for (int x = 0; x < 2; ++x)
+      if (!xs[x].compact) coop_put(A[x], v[x]);
+  }
   tc::fence_smem_for_async();
   do {
     // ---- [U_x | V_x] = p_x [P_x ; dP_x]' ----
     if (!(ok = tc_block_wait(&bar_tma, ptma, pend_tma, a.err))) break;
-    for (int i = 0; i < n_mma && ok; ++i) {
-      if (i == 1) {
-        put_row(A_hi, A_lo, tid, v);
-        tc::fence_smem_for_async();
-        __syncthreads();
-      }
+    const bool any_mma = !xs[0].compact || !xs[1].compact;
+    if (any_mma) {
       if (tid == 0) {
-        const int x = order[i];
-        tc::mma_split3<128>(tmem + 128 * x, smem_addr(A_hi), smem_addr(A_lo),
-                            smem_addr(C_hi[x]), smem_addr(C_lo[x]));
+        for (int x = 0; x < 2; ++x)
+          if (!xs[x].compact) {
+            uint32_t ta[3], tb[3];
+            term_addrs(A[x], kTerm128, ta);
+            term_addrs(Cm[x], kTerm128, tb);
+            tc::mma_split_bf16x3<128>(tmem + 128 * x, ta, tb);
+          }
         tc::commit(&bar_mma);
       }
-      ok = tc_block_wait(&bar_mma, pmma, pend_mma, a.err);
+      if (!(ok = tc_block_wait(&bar_mma, pmma, pend_mma, a.err))) break;
     }
-    if (!ok) break;
-    // A is free: stage Pt of the internal children for q_x = a_x P_x
+    // A is free: stage Pt of the internal children for q_x = a_x P_x, and
+    // the rows of q_k
     const bool any_int = xs[0].internal || xs[1].internal;
     if (any_int && tid == 0) {
-      mbar_expect_tx(&bar_tma, (xs[0].internal + xs[1].internal) * 2 * kTile64);
-      for (int x = 0; x < 2; ++x) {
-        if (!xs[x].internal) continue;
-        const unsigned char* src = unit_tiles(a, xs[x].b, r);
-        bulk_g2s(T_hi[x], src + kUnitPtHi, kTile64, &bar_tma);
-        bulk_g2s(T_lo[x], src + kUnitPtLo, kTile64, &bar_tma);
-      }
-    }
-    // exponent of this category's products at node k
-    int E = 0;
-    if (valid) {
-      if (!root) E += a.pre_escale[(kslot * R + r) * estr + c];
+      mbar_expect_tx(&bar_tma, (xs[0].internal + xs[1].internal) * kOp64);
       for (int x = 0; x < 2; ++x)
-        if (xs[x].internal) E += a.escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c];
+        if (xs[x].internal)
+          bulk_g2s(Tt[x], unit_tiles(a, xs[x].b, r) + kUnitPt, kOp64, &bar_tma);
     }
+    float* qst = reinterpret_cast<float*>(A[1]);
+    if (!root) coop_stage(qst, qv);
+    __syncthreads();
     // ---- epilogue 1: a_i, a_j, the Eq. 8 terms; a_x staged as an A operand ----
-    const float* qrow = (!root && valid) ? a.pre + ((kslot * C + c) * R + r) * 64 : nullptr;
     float ni = 0.f, nj = 0.f, dn = 0.f;
-#pragma unroll 1
-    for (int s0 = 0; s0 < 64; s0 += 16) {
-      float ui[16], vi[16], uj[16], vj[16], q[16];
-      child_chunk(xs[0], y[0], S, trow + 0 + s0, C_hi[0], C_lo[0], 128, 0, s0, ui);
-      child_chunk(xs[0], y[0], S, trow + 64 + s0, C_hi[0], C_lo[0], 128, 64, s0, vi);
-      child_chunk(xs[1], y[1], S, trow + 128 + s0, C_hi[1], C_lo[1], 128, 0, s0, uj);
-      child_chunk(xs[1], y[1], S, trow + 192 + s0, C_hi[1], C_lo[1], 128, 64, s0, vj);
-      if (xs[0].compact && y[0] >= S)
-        for (int i = 0; i < 16; ++i) vi[i] = 0.f;  // gap: d/dt of the all-ones vector
-      if (xs[1].compact && y[1] >= S)
-        for (int i = 0; i < 16; ++i) vj[i] = 0.f;
+    {
+      float q[32];
+      if (!root) {
 #pragma unroll
-      for (int i = 0; i < 16; i += 4) {
-        float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (qrow) {
-          qv = __ldg(reinterpret_cast<const float4*>(qrow + s0 + i));
-        } else if (root && valid) {
-          qv.x = s0 + i < S ? a.root_pit[s0 + i] : 0.f;
-          qv.y = s0 + i + 1 < S ? a.root_pit[s0 + i + 1] : 0.f;
-          qv.z = s0 + i + 2 < S ? a.root_pit[s0 + i + 2] : 0.f;
-          qv.w = s0 + i + 3 < S ? a.root_pit[s0 + i + 3] : 0.f;
+        for (int i = 0; i < 32; i += 4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(qst + row * kStageLd + 32 * h + i);
+          q[i] = t4.x; q[i + 1] = t4.y; q[i + 2] = t4.z; q[i + 3] = t4.w;
         }
-        q[i] = qv.x; q[i + 1] = qv.y; q[i + 2] = qv.z; q[i + 3] = qv.w;
-      }
-      float ai[16], aj[16];
+      } else {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        ai[i] = q[i] * uj[i];
-        aj[i] = q[i] * ui[i];
-        ni = fmaf(ai[i], vi[i], ni);
-        nj = fmaf(aj[i], vj[i], nj);
-        dn = fmaf(ai[i], ui[i], dn);
+        for (int i = 0; i < 32; ++i) q[i] = 32 * h + i < S ? a.root_pit[32 * h + i] : 0.f;
+      }
+      float ai[32], aj[32];
+      child_cols(xs[1], y[1], S, trow + 128 + 32 * h, Cm[1], kTerm128, 0, 32 * h, ai);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) ai[i] *= q[i];  // a_i = q o U_j
+      {
+        float ui[32];
+        child_cols(xs[0], y[0], S, trow + 0 + 32 * h, Cm[0], kTerm128, 0, 32 * h, ui);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          aj[i] = q[i] * ui[i];  // a_j = q o U_i
+          dn = fmaf(ai[i], ui[i], dn);
+        }
+      }
+      {
+        float vv[32];
+        if (!(xs[0].compact && y[0] >= S)) {  // a gap's d/dt of the all-ones vector is 0
+          child_cols(xs[0], y[0], S, trow + 64 + 32 * h, Cm[0], kTerm128, 64, 32 * h, vv);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) ni = fmaf(ai[i], vv[i], ni);
+        }
+        if (!(xs[1].compact && y[1] >= S)) {
+          child_cols(xs[1], y[1], S, trow + 192 + 32 * h, Cm[1], kTerm128, 64, 32 * h, vv);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) nj = fmaf(aj[i], vv[i], nj);
+        }
       }
       // a_x becomes the A operand of q_x = a_x P_x (the PdP tile of an
       // internal child is no longer read: its U, V came from TMEM)
 #pragma unroll
-      for (int i = 0; i < 16; i += 4) {
-        if (xs[0].internal)
-          tc::put_split4(C_hi[0], C_lo[0], tid, (s0 + i) >> 2, 128,
-                         make_float4(ai[i], ai[i + 1], ai[i + 2], ai[i + 3]));
-        if (xs[1].internal)
-          tc::put_split4(C_hi[1], C_lo[1], tid, (s0 + i) >> 2, 128,
-                         make_float4(aj[i], aj[i + 1], aj[i + 2], aj[i + 3]));
+      for (int g = 0; g < 4; ++g) {
+        if (xs[0].internal) {
+          const float x8[8] = {ai[8 * g], ai[8 * g + 1], ai[8 * g + 2], ai[8 * g + 3],
+                               ai[8 * g + 4], ai[8 * g + 5], ai[8 * g + 6], ai[8 * g + 7]};
+          tc::put_split3(Cm[0], Cm[0] + kTerm128, Cm[0] + 2 * kTerm128, row, 4 * h + g, x8);
+        }
+        if (xs[1].internal) {
+          const float x8[8] = {aj[8 * g], aj[8 * g + 1], aj[8 * g + 2], aj[8 * g + 3],
+                               aj[8 * g + 4], aj[8 * g + 5], aj[8 * g + 6], aj[8 * g + 7]};
+          tc::put_split3(Cm[1], Cm[1] + kTerm128, Cm[1] + 2 * kTerm128, row, 4 * h + g, x8);
+        }
       }
     }
-    if (valid) {
+    xch[h][0][row] = ni;
+    xch[h][1][row] = nj;
+    xch[h][2][row] = dn;
+    tc::fence_smem_for_async();
+    tc::fence_before();
+    __syncthreads();
+    if (valid && h == 0) {
       const float w = a.cat_wt[r];
       reinterpret_cast<float4*>(a.rterm)[(kslot * C + c) * R + r] =
-          make_float4(w * ni, w * nj, w * dn, __int_as_float(E));
+          make_float4(w * (ni + xch[1][0][row]), w * (nj + xch[1][1][row]),
+                      w * (dn + xch[1][2][row]), __int_as_float(E));
     }
     if (!any_int) break;
     // ---- q_x = a_x P_x for the internal children ----
-    tc::fence_smem_for_async();
-    tc::fence_before();
     if (!(ok = tc_block_wait(&bar_tma, ptma, pend_tma, a.err))) break;
     if (tid == 0) {
       for (int x = 0; x < 2; ++x)
-        if (xs[x].internal)
-          tc::mma_split3<64>(tmem + 64 * x, smem_addr(C_hi[x]), smem_addr(C_lo[x]),
-                             smem_addr(T_hi[x]), smem_addr(T_lo[x]));
+        if (xs[x].internal) {
+          uint32_t ta[3], tb[3];
+          term_addrs(Cm[x], kTerm128, ta);
+          term_addrs(Tt[x], kTerm64, tb);
+          tc::mma_split_bf16x3<64>(tmem + 64 * x, ta, tb);
+        }
       tc::commit(&bar_mma);
     }
     if (!(ok = tc_block_wait(&bar_mma, pmma, pend_mma, a.err))) break;
+    float qo[2][32];
+    for (int x = 0; x < 2; ++x) {
+      float m = 0.f;
+      if (xs[x].internal) {
+        tc::ld32(trow + 64 * x + 32 * h, qo[x]);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) m = fmaxf(m, fabsf(qo[x][i]));
+      }
+      xch[h][x][row] = m;
+    }
+    __syncthreads();
     for (int x = 0; x < 2; ++x) {
       if (!xs[x].internal) continue;
-      float qv[64];
-      float m = 0.f;
-#pragma unroll
-      for (int s0 = 0; s0 < 64; s0 += 16) {
-        float w16[16];
-        tc::ld16(trow + 64 * x + s0, w16);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          qv[s0 + i] = w16[i];
-          m = fmaxf(m, fabsf(w16[i]));
-        }
-      }
+      const float m = fmaxf(xch[0][x][row], xch[1][x][row]);
       int e = 0;
       if (valid) {
         if (!isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
         else if (m > 0.f) (void)frexpf(m, &e);
         e = max(e, -126);  // 2^-e stays finite for a subnormal maximum
       }
-      const float f = ldexpf(1.f, -e);
-      if (valid) {
-        const size_t slot = (size_t)(xs[x].b - a.n_tips);
-        float* out = a.pre + ((slot * C + c) * R + r) * 64;
-#pragma unroll
-        for (int i = 0; i < 64; i += 4)
-          *reinterpret_cast<float4*>(out + i) =
-              make_float4(qv[i] * f, qv[i + 1] * f, qv[i + 2] * f, qv[i + 3] * f);
-        // q_x = P_x' (q_k o U_sibling): exponents of q_k and of the sibling
-        const int sib = 1 - x;
-        int eq = e + (root ? 0 : a.pre_escale[(kslot * R + r) * estr + c]);
-        if (xs[sib].internal) eq += a.escale[((size_t)(xs[sib].b - a.n_tips) * R + r) * estr + c];
-        a.pre_escale[(slot * R + r) * estr + c] = eq;
-      }
+      stage_half(reinterpret_cast<float*>(A[1 - x]), row, h, qo[x], ldexpf(1.f, -e));
+      // q_x = P_x' (q_k o U_sibling): exponents of q_k and of the sibling
+      if (valid && h == 0)
+        a.pre_escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c] = e + eq_k + ep[1 - x];
     }
+    __syncthreads();
+    for (int x = 0; x < 2; ++x)
+      if (xs[x].internal)
+        coop_store(a.pre + ((size_t)(xs[x].b - a.n_tips) * C * R + r) * 64, (size_t)R * 64,
+                   c0, C, reinterpret_cast<const float*>(A[1 - x]));
   } while (false);
   if (tid == 0) {  // bounded drain of whatever a timeout left in flight
     if (pend_tma >= 0) (void)mbar_wait(&bar_tma, (uint32_t)pend_tma);
@@ -654,9 +796,9 @@ __global__ void __launch_bounds__(kTcThreads) pre_tc_kernel(LevelArgs<T> a) {
 // internal node, from the per-category terms of the pre-order kernels.
 // ---------------------------------------------------------------------------
 template <typename T>  // float only
-__global__ void __launch_bounds__(kTcThreads) ratio_tc_kernel(LevelArgs<T> a) {
+__global__ void __launch_bounds__(kTcRows) ratio_tc_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
-  __shared__ F2 red[kTcThreads / 32][2];
+  __shared__ F2 red[kTcRows / 32][2];
   const int R = a.n_cat, C = a.n_patterns;
   const size_t slot = blockIdx.y;
   const int2 ch = a.children[a.n_tips + (int)slot];
@@ -692,7 +834,7 @@ __global__ void __launch_bounds__(kTcThreads) ratio_tc_kernel(LevelArgs<T> a) {
       gj = Acc<float>::prod(W, Nj / Dn);
     }
   }
-  block_sum_acc<float, kTcThreads>(gi, gj, red, 1);
+  block_sum_acc<float, kTcRows>(gi, gj, red, 1);
   if (threadIdx.x == 0) {
     a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = Acc<float>::to_double(gi);
     a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = Acc<float>::to_double(gj);
@@ -715,7 +857,7 @@ template <typename T = float>
 inline cudaError_t launch_ratio_tc64(const LevelArgs<float>& a, cudaStream_t st) {
   if (a.n_tiles <= 0 || a.n_tips < 2) return cudaSuccess;
   dim3 grid(a.n_tiles, a.n_tips - 1);
-  ratio_tc_kernel<float><<<grid, kTcThreads, 0, st>>>(a);
+  ratio_tc_kernel<float><<<grid, kTcRows, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,7 @@ struct Layout {
   Region P, dP, post, pre, escale, pre_escale, rterm;
   Region tip_states, tip_partials, tip_has;
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
+  Region vsplit;  // tensor-core path: eigenvectors as double-float tables
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
   Region gpart, lpart, out;  // out = [logL, grad...] followed by the flag word
   size_t total = 0;
@@ -111,6 +112,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.pattern_w, (size_t)C * 8);
   ok &= add_region(L, L.V, (size_t)S * S * 8);
   ok &= add_region(L, L.Vinv, (size_t)S * S * 8);
+  if (tc) ok &= add_region(L, L.vsplit, kEigenSplitFloats * sizeof(float));
   ok &= add_region(L, L.lambda, (size_t)S * 8);
   ok &= add_region(L, L.pi, (size_t)S * 8);
   ok &= add_region(L, L.rates, (size_t)R * 8);
@@ -257,6 +259,7 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     e = cudaMemsetAsync(flag_word(ctx), 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     PmatArgs pa{};
+    pa.vsplit = ctx->L.vsplit.bytes ? ctx->dev<float>(ctx->L.vsplit) : nullptr;
     pa.V = ctx->dev<double>(ctx->L.V);
     pa.Vinv = ctx->dev<double>(ctx->L.Vinv);
     pa.lambda = ctx->dev<double>(ctx->L.lambda);
@@ -795,6 +798,12 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
   int rc;
   if ((rc = upload(ctx, ctx->L.V, V, (size_t)S * S, "upload V"))) return rc;
   if ((rc = upload(ctx, ctx->L.Vinv, Vinv, (size_t)S * S, "upload Vinv"))) return rc;
+  if (ctx->L.vsplit.bytes) {
+    std::vector<float> split(kEigenSplitFloats);
+    build_eigen_split(S, V, Vinv, split.data());
+    if ((rc = upload(ctx, ctx->L.vsplit, split.data(), split.size(), "upload V split"))) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  }
   if ((rc = upload(ctx, ctx->L.lambda, lambda, (size_t)S, "upload lambda"))) return rc;
   if ((rc = upload(ctx, ctx->L.pi, pi, (size_t)S, "upload pi"))) return rc;
   if ((rc = upload_typed(ctx, ctx->L.pi_t, pi, (size_t)S, "upload pi"))) return rc;

@@ -56,8 +56,25 @@ constexpr int kP4TilePatterns = PHYLO_P4_TILE;
 inline bool uses_tensor_cores(int SP, bool fp64) { return SP == 64 && !fp64; }
 constexpr int kTcTilePatterns = 128;
 // Matrix operand tiles of one (branch, category) on that path: [P; dP] and
-// P' as split TF32 pairs (kernels_tc64.cuh gives the layout).
-constexpr size_t kTcUnitBytes = 98304;
+// P' as three-term BF16 splits (kernels_tc64.cuh gives the layout).
+constexpr size_t kTcUnitBytes = 73728;
+
+// The eigenvectors as double-float pairs for the tensor-core path's matrix
+// kernel: out = [V' hi][V' lo][Vinv hi][Vinv lo], each 64 x 64 floats,
+// V' the transpose of V, zero outside S x S.
+constexpr size_t kEigenSplitFloats = 4 * 64 * 64;
+inline void build_eigen_split(int S, const double* V, const double* Vinv, float* out) {
+  for (int i = 0; i < (int)kEigenSplitFloats; ++i) out[i] = 0.f;
+  for (int m = 0; m < S; ++m)
+    for (int s = 0; s < S; ++s) {
+      const double v = V[s * S + m], w = Vinv[m * S + s];
+      const float vh = (float)v, wh = (float)w;
+      out[0 * 4096 + m * 64 + s] = vh;
+      out[1 * 4096 + m * 64 + s] = (float)(v - (double)vh);
+      out[2 * 4096 + m * 64 + s] = wh;
+      out[3 * 4096 + m * 64 + s] = (float)(w - (double)wh);
+    }
+}
 
 // Exponent planes per node: R on the tensor-core path, else 1 (one
 // exponent per (node, pattern) shared by all categories).
@@ -114,6 +131,7 @@ struct LevelArgs {
 };
 
 struct PmatArgs {
+  const float* vsplit;   // tensor-core path: build_eigen_split's table
   const double* V;       // [S][S]
   const double* Vinv;    // [S][S]
   const double* lambda;  // [S]

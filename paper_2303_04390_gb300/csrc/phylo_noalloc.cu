@@ -58,7 +58,7 @@ struct NaLayout {
   int SP = 0, RP = 0, n_tiles = 0;
   NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale,
       pre_escale, rterm;
-  NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
+  NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t, vsplit;
   NaRegion gpart, lpart, out, pattern_wt, cat_wt, pi_t;
   size_t total = 0;
 };
@@ -100,6 +100,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
   na_add(L, L.Vinv, (size_t)S * S * 8);
+  if (tc) na_add(L, L.vsplit, kEigenSplitFloats * sizeof(float));
   na_add(L, L.lambda, (size_t)S * 8);
   na_add(L, L.pi, (size_t)S * 8);
   na_add(L, L.rates, (size_t)R * 8);
@@ -298,6 +299,13 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   NA_TRY(up(L.pattern_w, pattern_weights, (size_t)C * 8), "upload weights");
   NA_TRY(up(L.V, V, (size_t)S * S * 8), "upload V");
   NA_TRY(up(L.Vinv, Vinv, (size_t)S * S * 8), "upload Vinv");
+  // static storage, not an allocation; the copy completes before this call
+  // returns (the stream is synchronised below)
+  static thread_local float vsplit[kEigenSplitFloats];
+  if (L.vsplit.bytes) {
+    build_eigen_split(S, V, Vinv, vsplit);
+    NA_TRY(up(L.vsplit, vsplit, sizeof(vsplit)), "upload V split");
+  }
   NA_TRY(up(L.lambda, lambda, (size_t)S * 8), "upload lambda");
   NA_TRY(up(L.pi, root_freqs, (size_t)S * 8), "upload pi");
   NA_TRY(up(L.rates, rates, (size_t)R * 8), "upload rates");
@@ -319,6 +327,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   NA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st), "clear flags");
 
   PmatArgs pa{};
+  pa.vsplit = L.vsplit.bytes ? reinterpret_cast<const float*>(ws + L.vsplit.off) : nullptr;
   pa.V = reinterpret_cast<const double*>(ws + L.V.off);
   pa.Vinv = reinterpret_cast<const double*>(ws + L.Vinv.off);
   pa.lambda = reinterpret_cast<const double*>(ws + L.lambda.off);
