@@ -399,6 +399,7 @@ post_small_kernel(LevelArgs<T> a) {
   const int rr = r < R ? r : 0;
   if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
   __syncthreads();
+  pdl_wait_and_release();
   int4 d[NPT];
 #pragma unroll
   for (int u = 0; u < NPT; ++u)
@@ -484,6 +485,7 @@ pre_small_kernel(LevelArgs<T> a) {
   const int rr = r < R ? r : 0;
   if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
   __syncthreads();
+  pdl_wait_and_release();
   int4 d[NPT];
 #pragma unroll
   for (int u = 0; u < NPT; ++u)
@@ -676,6 +678,7 @@ struct WideSmemPost {
 
 template <typename T>
 __global__ void __launch_bounds__(kWideThreads) post_wide_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();
   constexpr int CT = WideCfg<T>::CT;
   constexpr int NT = kWideThreads;
   constexpr int GROUPS = NT / kWideSP;  // 4
@@ -792,6 +795,7 @@ struct WideSmemPre {
 
 template <typename T>
 __global__ void __launch_bounds__(kWideThreads) pre_wide_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();
   constexpr int CT = WideCfg<T>::CT;
   constexpr int NT = kWideThreads;
   constexpr int GROUPS = NT / kWideSP;
@@ -967,14 +971,12 @@ cudaError_t launch_small(const LevelArgs<T>& a, bool post, cudaStream_t st) {
   constexpr int NPo = SmallNpt<T, SP>::post, NPr = SmallNpt<T, SP>::pre;
   if (post) {
     dim3 grid(a.n_tiles, (a.n_level + NPo - 1) / NPo);
-    post_small_kernel<T, SP, RP, NPo>
-        <<<grid, kSmallThreads, small_smem<T, SP, RP, NPo>(true), st>>>(a);
-  } else {
-    dim3 grid(a.n_tiles, (a.n_level + NPr - 1) / NPr);
-    pre_small_kernel<T, SP, RP, NPr>
-        <<<grid, kSmallThreads, small_smem<T, SP, RP, NPr>(false), st>>>(a);
+    return launch_pdl(post_small_kernel<T, SP, RP, NPo>, grid, kSmallThreads,
+                      small_smem<T, SP, RP, NPo>(true), st, a);
   }
-  return cudaGetLastError();
+  dim3 grid(a.n_tiles, (a.n_level + NPr - 1) / NPr);
+  return launch_pdl(pre_small_kernel<T, SP, RP, NPr>, grid, kSmallThreads,
+                    small_smem<T, SP, RP, NPr>(false), st, a);
 }
 
 template <typename T, int SP, int RP>
@@ -1027,10 +1029,9 @@ cudaError_t launch_level_impl(const LevelArgs<T>& a, int SP, int RP, bool post,
       } else {
         dim3 grid(a.n_tiles, a.n_level);
         if (post)
-          post_wide_kernel<T><<<grid, kWideThreads, wide_post_smem<T>(), st>>>(a);
-        else
-          pre_wide_kernel<T><<<grid, kWideThreads, wide_pre_smem<T>(a.n_cat), st>>>(a);
-        return cudaGetLastError();
+          return launch_pdl(post_wide_kernel<T>, grid, kWideThreads, wide_post_smem<T>(), st, a);
+        return launch_pdl(pre_wide_kernel<T>, grid, kWideThreads, wide_pre_smem<T>(a.n_cat), st,
+                          a);
       }
     default: return cudaErrorInvalidValue;
   }

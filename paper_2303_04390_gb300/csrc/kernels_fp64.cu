@@ -11,6 +11,7 @@ namespace phylo {
 // deterministic.  Output 0 is log P(Y); output 1 + b is the gradient of
 // branch b.
 __global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
+  pdl_wait_and_release();
   const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (warp > a.n_branches) return;  // warp-uniform
@@ -27,8 +28,7 @@ __global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
   const int warps = a.n_branches + 1;
   const int blocks = (warps * 32 + 255) / 256;
-  reduce_kernel<<<blocks, 256, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(reduce_kernel, dim3(blocks), dim3(256), 0, st, a);
 }
 
 }  // namespace phylo

@@ -111,6 +111,7 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
   const uint32_t mbytes = (uint32_t)R * 64;
   if (tid == 0) mbar_init_fenced(&bar, 1);
   __syncthreads();
+  pdl_wait_and_release();
   if (tid == 0) {
     mbar_expect_tx(&bar, mbytes * (PRE ? 4 : 2));
     bulk_g2s(sm.raw[0], a.P + (size_t)bi * R * 16, mbytes, &bar);
@@ -316,11 +317,8 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
 template <int RM>
 cudaError_t launch_p4(const LevelArgs<float>& a, bool post, cudaStream_t st) {
   dim3 grid(a.n_tiles, a.n_level);
-  if (post)
-    level_p4_kernel<RM, false><<<grid, kP4Threads, 0, st>>>(a);
-  else
-    level_p4_kernel<RM, true><<<grid, kP4Threads, 0, st>>>(a);
-  return cudaGetLastError();
+  if (post) return launch_pdl(level_p4_kernel<RM, false>, grid, kP4Threads, 0, st, a);
+  return launch_pdl(level_p4_kernel<RM, true>, grid, kP4Threads, 0, st, a);
 }
 
 // RP (next power of two >= R) selects the unrolled category count.

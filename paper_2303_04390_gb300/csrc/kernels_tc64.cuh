@@ -402,6 +402,7 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
 template <typename T>  // float only
 __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
+  pdl_wait_and_release();  // before TMEM, smem or any global access
   static_assert(kStageBytes <= kOp128, "staging fits in an operand buffer");
   extern __shared__ unsigned char smraw[];
   unsigned char* base = align1024(smraw);
@@ -573,6 +574,7 @@ __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
 template <typename T>  // float only
 __global__ void __launch_bounds__(kTcThreads) pre_tc_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
+  pdl_wait_and_release();  // before TMEM, smem or any global access
   static_assert(kStageBytes + 0 <= kOp128 && 2 * kOp64 <= kOp128, "buffer reuse fits");
   extern __shared__ unsigned char smraw[];
   unsigned char* base = align1024(smraw);
@@ -798,6 +800,7 @@ __global__ void __launch_bounds__(kTcThreads) pre_tc_kernel(LevelArgs<T> a) {
 template <typename T>  // float only
 __global__ void __launch_bounds__(kTcRows) ratio_tc_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
+  pdl_wait_and_release();  // before TMEM, smem or any global access
   __shared__ F2 red[kTcRows / 32][2];
   const int R = a.n_cat, C = a.n_patterns;
   const size_t slot = blockIdx.y;
@@ -845,20 +848,17 @@ template <typename T = float>
 inline cudaError_t launch_tc64(const LevelArgs<float>& a, bool post, cudaStream_t st) {
   if (post) {
     dim3 grid(a.n_tiles, a.n_level, a.root_level ? 1 : a.n_cat);
-    post_tc_kernel<float><<<grid, kTcThreads, kTcPostSmem, st>>>(a);
-  } else {
-    dim3 grid(a.n_tiles, a.n_level, a.n_cat);
-    pre_tc_kernel<float><<<grid, kTcThreads, kTcPreSmem, st>>>(a);
+    return launch_pdl(post_tc_kernel<float>, grid, kTcThreads, kTcPostSmem, st, a);
   }
-  return cudaGetLastError();
+  dim3 grid(a.n_tiles, a.n_level, a.n_cat);
+  return launch_pdl(pre_tc_kernel<float>, grid, kTcThreads, kTcPreSmem, st, a);
 }
 
 template <typename T = float>
 inline cudaError_t launch_ratio_tc64(const LevelArgs<float>& a, cudaStream_t st) {
   if (a.n_tiles <= 0 || a.n_tips < 2) return cudaSuccess;
   dim3 grid(a.n_tiles, a.n_tips - 1);
-  ratio_tc_kernel<float><<<grid, kTcRows, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_pdl(ratio_tc_kernel<float>, grid, kTcRows, 0, st, a);
 }
 
 template <typename T = float>

@@ -150,6 +150,29 @@ struct ReduceArgs {
   double* out;           // [1 + n_branches]
 };
 
+// Launch with programmatic stream serialisation: the kernel may begin
+// launching while its predecessor drains; every kernel launched this way
+// starts with pdl_wait_and_release() (tma.cuh) before it touches memory
+// that other kernels write.  PHYLO_PDL=0 at build time turns it off.
+#ifndef PHYLO_PDL
+#define PHYLO_PDL 1
+#endif
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = PHYLO_PDL;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Launchers (kernels_fp32.cu / kernels_fp64.cu).  SP = padded states.
 template <typename T>
 cudaError_t launch_pmat(const PmatArgs& a, int SP, cudaStream_t st);

@@ -58,4 +58,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src,
       : "memory");
 }
 
+// Programmatic dependent launch: wait until the kernel before this one in
+// the stream has completed with its writes visible, then let the kernel
+// after this one start launching its CTAs (they wait the same way before
+// touching memory).  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace phylo
