@@ -66,11 +66,25 @@ __device__ __forceinline__ float max4(float2 lo, float2 hi) {
 
 // Shared layout of one block: for each staged matrix block m (R x 16
 // floats, category-major) a raw copy and its per-category transpose.
-template <int RM>
+//   m = 0..3:  P_i, P_j, dP_i, dP_j
+//   m = 4..7:  P of the tip branches below a cherry child (i: 4, 5; j: 6, 7)
+template <int NM, int RM>
 struct P4Mats {
-  float4 raw[4][RM * 4];  // P_i, P_j, dP_i, dP_j as copied (rows)
-  float4 tr[4][RM * 4];   // their transposes (rows of M' = columns of M)
+  float4 raw[NM][RM * 4];  // as copied (rows)
+  float4 tr[NM][RM * 4];   // transposes (rows of M' = columns of M)
 };
+
+// Cherry fusion.  A cherry is a non-root internal node whose two children
+// are tips with compact states.  It gets no post-order launch and stores no
+// partials: wherever its partials are needed (its parent's post- and
+// pre-order steps) they are formed as p_x = (P_xa e_ya) o (P_xb e_yb) from
+// the two tip states (no rescale is needed: both factors are transition
+// probabilities).  This removes the write of p_x and its two read-backs.
+// The cherry keeps its own pre-order step.
+__device__ __forceinline__ float4 p4_col(const float4* T, int y, int S) {
+  if (y < S) return T[y];
+  return make_float4(1.f, S > 1 ? 1.f : 0.f, S > 2 ? 1.f : 0.f, S > 3 ? 1.f : 0.f);
+}
 
 // The child's 4 states for category r: u = M v (and w = dM v), a compact
 // state selecting a column (gap: all ones, w = 0).
@@ -95,9 +109,17 @@ __device__ __forceinline__ void p4_child(int y, int S, float4 v,
   if (WITH_D) mv4t(DT, v, wlo, whi);
 }
 
-template <int RM, bool PRE>
-__global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a) {
-  __shared__ P4Mats<RM> sm;
+// The pre-order kernel is latency-bound at these occupancies: asking for 12
+// resident blocks per SM (at most 85 registers a thread) measured 4% faster
+// than the unbounded register allocation; the post-order kernel is left
+// unbounded.
+constexpr int kP4PreMinBlocks = 12;
+
+template <int RM, bool PRE, bool CH>
+__global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
+    level_p4_kernel(LevelArgs<float> a) {
+  constexpr int NM = CH ? 8 : 4;
+  __shared__ P4Mats<NM, RM> sm;
   __shared__ uint64_t bar;
   __shared__ F2 red[kP4Threads / 32][2];
   __shared__ double lred[kP4Threads / 32];
@@ -106,6 +128,9 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
   const int4 d = a.level_desc[blockIdx.y];
   const int k = d.x, bi = d.y, bj = d.z;
   const bool ci = d.w & kDescFlagCompact0, cj = d.w & kDescFlagCompact1;
+  const bool hi_ = CH && (d.w & kDescFlagCherry0), hj_ = CH && (d.w & kDescFlagCherry1);
+  const int2 gi2 = hi_ ? a.children[bi] : make_int2(0, 0);  // tips below a cherry
+  const int2 gj2 = hj_ ? a.children[bj] : make_int2(0, 0);
   const int c = blockIdx.x * kP4Threads + tid;
   const bool valid = c < C;
   const uint32_t mbytes = (uint32_t)R * 64;
@@ -113,31 +138,49 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
   __syncthreads();
   pdl_wait_and_release();
   if (tid == 0) {
-    mbar_expect_tx(&bar, mbytes * (PRE ? 4 : 2));
+    const int n_ch = (int)hi_ + (int)hj_;
+    mbar_expect_tx(&bar, mbytes * ((PRE ? 4 : 2) + 2 * n_ch));
     bulk_g2s(sm.raw[0], a.P + (size_t)bi * R * 16, mbytes, &bar);
     bulk_g2s(sm.raw[1], a.P + (size_t)bj * R * 16, mbytes, &bar);
     if (PRE) {
       bulk_g2s(sm.raw[2], a.dP + (size_t)bi * R * 16, mbytes, &bar);
       bulk_g2s(sm.raw[3], a.dP + (size_t)bj * R * 16, mbytes, &bar);
     }
+    if constexpr (CH) {
+      for (int x = 0; x < 2; ++x) {
+        if (!(x == 0 ? hi_ : hj_)) continue;
+        const int2 g = x == 0 ? gi2 : gj2;
+        bulk_g2s(sm.raw[4 + 2 * x], a.P + (size_t)g.x * R * 16, mbytes, &bar);
+        bulk_g2s(sm.raw[5 + 2 * x], a.P + (size_t)g.y * R * 16, mbytes, &bar);
+      }
+    }
   }
   // ---- every global load of this pattern, issued before any use ----------
   float4 vi[RM], vj[RM], q[RM];
   int yi = -1, yj = -1, ei = 0, ej = 0;
+  int ya[2] = {0, 0}, yb[2] = {0, 0};  // tip states below cherry children
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (valid) {
     if (ci) yi = a.tip_states[(size_t)bi * a.state_stride + c];
     if (cj) yj = a.tip_states[(size_t)bj * a.state_stride + c];
+    if (hi_) {
+      ya[0] = a.tip_states[(size_t)gi2.x * a.state_stride + c];
+      yb[0] = a.tip_states[(size_t)gi2.y * a.state_stride + c];
+    }
+    if (hj_) {
+      ya[1] = a.tip_states[(size_t)gj2.x * a.state_stride + c];
+      yb[1] = a.tip_states[(size_t)gj2.y * a.state_stride + c];
+    }
   }
 #pragma unroll
   for (int r = 0; r < RM; ++r) {
     const bool on = valid && r < R;
     vi[r] = zero4; vj[r] = zero4; q[r] = zero4;
-    if (on && !ci)
+    if (on && !ci && !hi_)
       vi[r] = bi < a.n_tips ? __ldg(reinterpret_cast<const float4*>(a.tip_partials) + (size_t)bi * C + c)
                             : __ldg(reinterpret_cast<const float4*>(a.post) +
                                     ((size_t)(bi - a.n_tips) * C + c) * R + r);
-    if (on && !cj)
+    if (on && !cj && !hj_)
       vj[r] = bj < a.n_tips ? __ldg(reinterpret_cast<const float4*>(a.tip_partials) + (size_t)bj * C + c)
                             : __ldg(reinterpret_cast<const float4*>(a.post) +
                                     ((size_t)(bj - a.n_tips) * C + c) * R + r);
@@ -145,9 +188,9 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
       q[r] = __ldg(reinterpret_cast<const float4*>(a.pre) +
                    ((size_t)(k - a.n_tips) * C + c) * R + r);
   }
-  if (!PRE && valid) {
-    if (bi >= a.n_tips) ei = a.escale[(size_t)(bi - a.n_tips) * a.escale_stride + c];
-    if (bj >= a.n_tips) ej = a.escale[(size_t)(bj - a.n_tips) * a.escale_stride + c];
+  if (!PRE && valid) {  // a cherry's exponent is 0 (its partials are not rescaled)
+    if (bi >= a.n_tips && !hi_) ei = a.escale[(size_t)(bi - a.n_tips) * a.escale_stride + c];
+    if (bj >= a.n_tips && !hj_) ej = a.escale[(size_t)(bj - a.n_tips) * a.escale_stride + c];
   }
   // ---- matrices: wait for the bulk copies, transpose once per block ------
   if (!__syncthreads_and(mbar_wait(&bar, 0))) {
@@ -157,14 +200,31 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
   {
     const float* raw = reinterpret_cast<const float*>(sm.raw);
     float* tr = reinterpret_cast<float*>(sm.tr);
-    const int n = (PRE ? 4 : 2) * RM * 16;
+    const int nm = PRE ? 4 : 2, n = (nm + (hi_ || hj_ ? 4 : 0)) * RM * 16;
     for (int i = tid; i < n; i += kP4Threads) {
-      const int m = i / (RM * 16), rem = i % (RM * 16), rr = rem / 16, e = rem % 16;
+      int m = i / (RM * 16);
+      const int rem = i % (RM * 16), rr = rem / 16, e = rem % 16;
+      if (m >= nm) m += 4 - nm;  // the grandchildren's blocks sit at 4..7
       const int s = e / 4, t = e % 4;  // tr[m][rr][t][s] = raw[m][rr][s][t]
       tr[(m * RM + rr) * 16 + t * 4 + s] = raw[(m * RM + rr) * 16 + s * 4 + t];
     }
   }
   __syncthreads();
+  if constexpr (CH) {
+    // a cherry child's partials from its two tip states
+#pragma unroll
+    for (int r = 0; r < RM; ++r) {
+      if (!(valid && r < R)) continue;
+      if (hi_) {
+        const float4 u = p4_col(sm.tr[4] + r * 4, ya[0], S), w = p4_col(sm.tr[5] + r * 4, yb[0], S);
+        vi[r] = make_float4(u.x * w.x, u.y * w.y, u.z * w.z, u.w * w.w);
+      }
+      if (hj_) {
+        const float4 u = p4_col(sm.tr[6] + r * 4, ya[1], S), w = p4_col(sm.tr[7] + r * 4, yb[1], S);
+        vj[r] = make_float4(u.x * w.x, u.y * w.y, u.z * w.z, u.w * w.w);
+      }
+    }
+  }
   if (!PRE) {
     // ---- Eq. 2: p_k = (P_i p_i) o (P_j p_j) for every category ------------
     float2 plo[RM], phi[RM];
@@ -317,8 +377,12 @@ __global__ void __launch_bounds__(kP4Threads) level_p4_kernel(LevelArgs<float> a
 template <int RM>
 cudaError_t launch_p4(const LevelArgs<float>& a, bool post, cudaStream_t st) {
   dim3 grid(a.n_tiles, a.n_level);
-  if (post) return launch_pdl(level_p4_kernel<RM, false>, grid, kP4Threads, 0, st, a);
-  return launch_pdl(level_p4_kernel<RM, true>, grid, kP4Threads, 0, st, a);
+  if (a.level_cherry) {
+    if (post) return launch_pdl(level_p4_kernel<RM, false, true>, grid, kP4Threads, 0, st, a);
+    return launch_pdl(level_p4_kernel<RM, true, true>, grid, kP4Threads, 0, st, a);
+  }
+  if (post) return launch_pdl(level_p4_kernel<RM, false, false>, grid, kP4Threads, 0, st, a);
+  return launch_pdl(level_p4_kernel<RM, true, false>, grid, kP4Threads, 0, st, a);
 }
 
 // RP (next power of two >= R) selects the unrolled category count.

@@ -153,6 +153,9 @@ struct phylo_ctx {
   std::vector<int2> children;
   std::vector<int> post_nodes, post_off;  // level l: [post_off[l], post_off[l+1])
   std::vector<int> pre_nodes, pre_off;
+  std::vector<char> post_cherry, pre_cherry;  // per level: a node has a fused cherry child
+  std::vector<int> height, depth;             // per node
+  std::vector<char> cherry;                   // per node: fused into its parent
   std::vector<int> tip_has;
   bool have_tree = false, have_states = false, have_weights = false,
        have_eigen = false, have_cats = false, have_t = false;
@@ -284,6 +287,7 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
       a.level_desc = desc + off[l];
       a.n_level = off[l + 1] - off[l];
       a.root_level = post && l + 2 == off.size();  // the last post level is the root
+      a.level_cherry = (post ? ctx->post_cherry : ctx->pre_cherry)[l];
       e = post ? launch_post_level<T>(a, ctx->L.SP, ctx->L.RP, st)
                : launch_pre_level<T>(a, ctx->L.SP, ctx->L.RP, st);
       if (e != cudaSuccess) return e;
@@ -370,6 +374,63 @@ int upload(phylo_ctx* ctx, const Region& r, const T* host, size_t count,
 
 // Level-node descriptors {k, child 0, child 1, flags} for both passes; the
 // flags depend on which tips carry partial vectors.
+// Level lists: post-order by height, pre-order by depth, one launch per
+// non-empty level.  On the FP32 4-state path a cherry (a non-root node
+// whose children are both tips with compact states) is fused into its
+// parent's post-order launch (kernels_p4.cuh) and gets no post-order level
+// entry of its own.
+int build_schedule(phylo_ctx* ctx) {
+  const int N = ctx->N, n = 2 * N - 1, root = n - 1;
+  const bool fuse = ctx->precision == PHYLO_FP32 && ctx->L.SP == 4;
+  const std::vector<int2>& ch = ctx->children;
+  ctx->cherry.assign(n, 0);
+  if (fuse)
+    for (int v = N; v < root; ++v)
+      ctx->cherry[v] = ch[v].x < N && ch[v].y < N && !ctx->tip_has[ch[v].x] &&
+                       !ctx->tip_has[ch[v].y];
+  auto has_cherry_child = [&](int v) {
+    return (ch[v].x >= N && ctx->cherry[ch[v].x]) || (ch[v].y >= N && ctx->cherry[ch[v].y]);
+  };
+  int H = 0, D = 0;
+  for (int v = N; v < n; ++v) {
+    H = ctx->height[v] > H ? ctx->height[v] : H;
+    D = ctx->depth[v] > D ? ctx->depth[v] : D;
+  }
+  std::vector<std::vector<int>> by_height(H + 1), by_depth(D + 1);
+  for (int v = N; v < n; ++v) {
+    if (!ctx->cherry[v]) by_height[ctx->height[v]].push_back(v);
+    by_depth[ctx->depth[v]].push_back(v);
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int>& nodes = pass == 0 ? ctx->post_nodes : ctx->pre_nodes;
+    std::vector<int>& off = pass == 0 ? ctx->post_off : ctx->pre_off;
+    std::vector<char>& flag = pass == 0 ? ctx->post_cherry : ctx->pre_cherry;
+    const std::vector<std::vector<int>>& lv = pass == 0 ? by_height : by_depth;
+    nodes.clear();
+    off.assign(1, 0);
+    flag.clear();
+    for (const std::vector<int>& level : lv) {
+      if (level.empty()) continue;
+      char any = 0;
+      for (int v : level) {
+        nodes.push_back(v);
+        any |= has_cherry_child(v);
+      }
+      off.push_back((int)nodes.size());
+      flag.push_back(any);
+    }
+  }
+  int rc = upload(ctx, ctx->L.post_nodes, ctx->post_nodes.data(), ctx->post_nodes.size(),
+                  "upload schedule");
+  if (rc) return rc;
+  rc = upload(ctx, ctx->L.pre_nodes, ctx->pre_nodes.data(), ctx->pre_nodes.size(),
+              "upload schedule");
+  if (rc) return rc;
+  // the pageable uploads above must complete before the host vectors change
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  return PHYLO_OK;
+}
+
 int upload_descriptors(phylo_ctx* ctx) {
   for (int pass = 0; pass < 2; ++pass) {
     const std::vector<int>& nodes = pass == 0 ? ctx->post_nodes : ctx->pre_nodes;
@@ -380,6 +441,8 @@ int upload_descriptors(phylo_ctx* ctx) {
       int flags = 0;
       if (ch.x < ctx->N && !ctx->tip_has[ch.x]) flags |= kDescFlagCompact0;
       if (ch.y < ctx->N && !ctx->tip_has[ch.y]) flags |= kDescFlagCompact1;
+      if (ch.x >= ctx->N && ctx->cherry[ch.x]) flags |= kDescFlagCherry0;
+      if (ch.y >= ctx->N && ctx->cherry[ch.y]) flags |= kDescFlagCherry1;
       desc[i] = make_int4(k, ch.x, ch.y, flags);
     }
     if (!desc.empty()) {
@@ -656,34 +719,13 @@ int phylo_set_tree(phylo_ctx* ctx, const int32_t* parent) {
         const int a = height[ch[v].x], b = height[ch[v].y];
         height[v] = 1 + (a > b ? a : b);
       }
-  const int H = height[root];
-  std::vector<std::vector<int>> by_height(H + 1);
-  for (int v = N; v < n; ++v) by_height[height[v]].push_back(v);
-  ctx->post_nodes.clear();
-  ctx->post_off.assign(1, 0);
-  for (int h = 1; h <= H; ++h) {
-    for (int v : by_height[h]) ctx->post_nodes.push_back(v);
-    ctx->post_off.push_back((int)ctx->post_nodes.size());
-  }
-  ctx->pre_nodes.clear();
-  ctx->pre_off.assign(1, 0);
-  for (int d = 0; d <= max_depth; ++d) {
-    bool any = false;
-    for (int v : by_depth[d])
-      if (v >= N) { ctx->pre_nodes.push_back(v); any = true; }
-    if (any) ctx->pre_off.push_back((int)ctx->pre_nodes.size());
-  }
   ctx->children = ch;
+  ctx->height = height;
+  ctx->depth = depth;
   int rc = upload(ctx, ctx->L.children, ch.data(), ch.size(), "upload tree");
   if (rc) return rc;
-  rc = upload(ctx, ctx->L.post_nodes, ctx->post_nodes.data(), ctx->post_nodes.size(),
-              "upload schedule");
-  if (rc) return rc;
-  rc = upload(ctx, ctx->L.pre_nodes, ctx->pre_nodes.data(), ctx->pre_nodes.size(),
-              "upload schedule");
-  if (rc) return rc;
-  // the pageable uploads above must complete before the host vectors change
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  if ((rc = build_schedule(ctx))) return rc;
   invalidate_graph(ctx);
   ctx->have_tree = true;
   return PHYLO_OK;
@@ -751,7 +793,10 @@ int phylo_set_tip_partials(phylo_ctx* ctx, int tip, const double* partials) {
                   "upload tip flags");
   if (rc) return rc;
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
-  if (!was) invalidate_graph(ctx);  // kernels now take the partials path
+  if (!was) {  // kernels now take the partials path; a cherry above it is no longer fused
+    invalidate_graph(ctx);
+    if (ctx->have_tree && (rc = build_schedule(ctx))) return rc;
+  }
   return PHYLO_OK;
 }
 

@@ -10,8 +10,10 @@
 namespace phylo {
 
 // Flags of a level-node descriptor: child 0 / child 1 is a tip with a
-// compact state.
+// compact state; child 0 / child 1 is a cherry fused into this node (FP32,
+// 4 states: kernels_p4.cuh).
 constexpr int kDescFlagCompact0 = 1, kDescFlagCompact1 = 2;
+constexpr int kDescFlagCherry0 = 4, kDescFlagCherry1 = 8;
 
 // Device-side numeric flags (bit mask in the workspace's error word).
 enum : int {
@@ -100,6 +102,7 @@ struct LevelArgs {
   const int4* level_desc;      // per level node: {k, child 0, child 1, flags}
   int n_level;                 // number of nodes in the level
   int root_level;              // 1 if the level is the root alone
+  int level_cherry;            // 1 if a node of the level has a fused cherry child
   int n_tips, n_patterns, n_states, n_cat, root;
   const T* P;                  // [2N-2][R][SP][SP], row = parent state
                                // (tensor-core path: [2N-2][R] operand tiles)

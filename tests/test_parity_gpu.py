@@ -194,11 +194,13 @@ def test_deterministic_and_stream_ordered():
 
 
 def test_launch_count_matches_level_schedule():
+    """One launch per non-empty level.  On the FP32 4-state path a cherry
+    (non-root node whose two children are tips) is fused into its parent's
+    post-order step and has no post-order level of its own."""
     import paper_2303_04390_gb300 as pg
     from oracle import phylo_oracle as O
     for tree in ["yule", "caterpillar", "balanced"]:
         w = synth.small_workload(33, 4, 2, 40, seed=29, tree=tree)
-        ctx = pg.from_workload(w, "fp32")
         kids, root = O.tree_children(w.parent)
         height = {}
         for v in O.postorder_list(w.parent):
@@ -207,8 +209,17 @@ def test_launch_count_matches_level_schedule():
         for v in reversed(O.postorder_list(w.parent)):
             for c in kids[v]:
                 depth[c] = depth[v] + 1
-        n_pre = len({depth[v] for v in range(w.n_tips, len(w.parent))})
-        assert ctx.launches_per_evaluation() == 2 + height[root] + n_pre
+        internal = range(w.n_tips, len(w.parent))
+        cherry = {v for v in internal
+                  if v != root and all(c < w.n_tips for c in kids[v])}
+        for precision, fused in (("fp32", cherry), ("fp64", set())):
+            ctx = pg.from_workload(w, precision)
+            keep = [v for v in internal if v not in fused]
+            n_post = len({height[v] for v in keep})
+            n_pre = len({depth[v] for v in internal})
+            assert ctx.launches_per_evaluation() == 2 + n_post + n_pre, (tree, precision)
+            assert ctx.level_counts() == (n_post, n_pre)
+            ctx.close()
 
 
 FULL = {
