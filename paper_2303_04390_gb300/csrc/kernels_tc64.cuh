@@ -68,6 +68,8 @@ static_assert(kTcUnitBytes == kOp128 + kOp64, "matrix tile block size");
 //   pre:  A_i, A_j (48 KB each; later Pt_i, Pt_j) | PdP_i, PdP_j (48 KB
 //         each; later a_i, a_j as A operands)
 constexpr size_t kTcPostSmem = 1024 + 2 * kOp128 + 2 * kOp64;
+//   pipelined post: A_i, A_j | B for the current and the next item
+constexpr size_t kTcPipePostSmem = 1024 + 2 * kOp128 + 4 * kOp64;
 constexpr size_t kTcPreSmem = 1024 + 4 * kOp128;
 
 __device__ __forceinline__ float pow2i(int d) {  // 2^d for d <= 0 (0 below 2^-126)
@@ -569,6 +571,208 @@ __global__ void __launch_bounds__(kTcThreads) post_tc_kernel(LevelArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
+// Persistent, pipelined post-order levels.  One CTA per SM walks the
+// level's items (node, 128-pattern tile, category) i = blockIdx.x,
+// + gridDim.x, ...; while item i's contractions and epilogue run, the next
+// item's partial rows are already loading into registers and its matrix
+// tiles into the second shared buffer.  (The root level keeps
+// post_tc_kernel above: one node, whose CTAs loop over the categories to
+// form log L_c.)
+// ---------------------------------------------------------------------------
+struct TcItem {
+  int k, c0, r;
+  TcChild xs[2];
+};
+
+__device__ __forceinline__ TcItem tc_item(const LevelArgs<float>& a, int i) {
+  TcItem it;
+  it.r = i % a.n_cat;
+  const int rest = i / a.n_cat;
+  it.c0 = (rest % a.n_tiles) * kTcRows;
+  const int4 d = a.level_desc[rest / a.n_tiles];
+  it.k = d.x;
+  it.xs[0] = tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0);
+  it.xs[1] = tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1);
+  return it;
+}
+
+// Bounded wait agreed by the whole block; the parity advances only on
+// success, so after a timeout it still names the phase in flight.
+__device__ __forceinline__ bool tc_wait_phase(uint64_t* bar, uint32_t& parity, int* err) {
+  const bool ok = __syncthreads_and(mbar_wait(bar, parity));
+  if (ok) parity ^= 1u;
+  else if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+  tc::fence_after();
+  return ok;
+}
+
+// What one thread loads ahead for an item: both children's rows (in the
+// cooperative layout), its pattern's compact tip states and the children's
+// post-order exponents.
+struct TcPrefetch {
+  float4 v[2][8];
+  int y[2], ep[2];
+};
+
+__device__ __forceinline__ void tc_prefetch(const LevelArgs<float>& a, const TcItem& it, int row,
+                                            TcPrefetch& pf) {
+  const int C = a.n_patterns, c = it.c0 + row;
+  const bool valid = c < C;
+#pragma unroll
+  for (int x = 0; x < 2; ++x) {
+    pf.y[x] = 0;
+    pf.ep[x] = 0;
+    if (it.xs[x].compact) {
+      if (valid) pf.y[x] = a.tip_states[(size_t)it.xs[x].b * a.state_stride + c];
+    } else {
+      size_t stride;
+      const float* src = child_base(a, it.xs[x], it.r, &stride);
+      coop_load(pf.v[x], src, stride, it.c0, C);
+      if (it.xs[x].internal && valid)
+        pf.ep[x] = a.escale[((size_t)(it.xs[x].b - a.n_tips) * a.n_cat + it.r) *
+                                a.escale_stride + c];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Post-order level (Eq. 2), every level but the root's
+// ---------------------------------------------------------------------------
+template <typename T>  // float only
+__global__ void __launch_bounds__(kTcThreads) post_tc_pipe_kernel(LevelArgs<T> a) {
+  static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
+  pdl_wait_and_release();  // before TMEM, smem or any global access
+  extern __shared__ unsigned char smraw[];
+  unsigned char* base = align1024(smraw);
+  unsigned char* A[2] = {base, base + kOp128};
+  // B[buffer][child]: P_x of the current item, and of the next one
+  unsigned char* B[2][2] = {{base + 2 * kOp128, base + 2 * kOp128 + kOp64},
+                            {base + 2 * kOp128 + 2 * kOp64, base + 2 * kOp128 + 3 * kOp64}};
+  float* stage = reinterpret_cast<float*>(A[0]);  // output rows, after the MMAs
+  __shared__ uint64_t bar_tma[2], bar_mma;
+  __shared__ uint32_t tmem_slot;
+  __shared__ float xch[2][kTcRows];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kTcRows - 1), h = tid / kTcRows;
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int n_items = a.n_level * a.n_tiles * R;
+  int i = blockIdx.x;
+  if (i >= n_items) return;  // block-uniform, before any allocation
+  if (warp == 0) tc::alloc(&tmem_slot, 128);
+  if (tid == 0) {
+    mbar_init_fenced(&bar_tma[0], 1);
+    mbar_init_fenced(&bar_tma[1], 1);
+    mbar_init_fenced(&bar_mma, 1);
+  }
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+  uint32_t ptma[2] = {0, 0}, pmma = 0;
+  bool tpend[2] = {false, false}, mpend = false;
+  auto issue_b = [&](const TcItem& it, int buf) {
+    if (tid == 0) {
+      mbar_expect_tx(&bar_tma[buf], 2 * kOp64);
+      for (int x = 0; x < 2; ++x) {
+        const unsigned char* src = unit_tiles(a, it.xs[x].b, it.r) + kUnitPdp;
+        for (int t = 0; t < 3; ++t)  // rows 0..63 (P) of each term of the PdP operand
+          bulk_g2s(B[buf][x] + t * kTerm64, src + t * kTerm128, kTerm64, &bar_tma[buf]);
+      }
+    }
+    tpend[buf] = true;
+  };
+  TcItem it = tc_item(a, i);
+  issue_b(it, 0);
+  TcPrefetch pf;
+  tc_prefetch(a, it, row, pf);
+  int buf = 0;
+  for (;;) {
+    const TcItem cur = it;
+    const int y0 = pf.y[0], y1 = pf.y[1];
+    int E = pf.ep[0] + pf.ep[1];
+    const int c = cur.c0 + row;
+    const bool valid = c < C;
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+      if (!cur.xs[x].compact) coop_put(A[x], pf.v[x]);
+    tc::fence_smem_for_async();
+    if (!tc_wait_phase(&bar_tma[buf], ptma[buf], a.err)) break;
+    tpend[buf] = false;
+    const bool any_mma = !cur.xs[0].compact || !cur.xs[1].compact;
+    if (any_mma) {
+      if (tid == 0) {
+        for (int x = 0; x < 2; ++x)
+          if (!cur.xs[x].compact)
+            {
+              uint32_t ta[3], tb[3];
+              term_addrs(A[x], kTerm128, ta);
+              term_addrs(B[buf][x], kTerm64, tb);
+              tc::mma_split_bf16x3<64>(tmem + 64 * x, ta, tb);
+            }
+        tc::commit(&bar_mma);
+      }
+      mpend = true;
+    }
+    // the next item's matrices and rows load while this one computes
+    const int inext = i + (int)gridDim.x;
+    const bool more = inext < n_items;
+    if (more) {
+      it = tc_item(a, inext);
+      issue_b(it, buf ^ 1);
+      tc_prefetch(a, it, row, pf);
+    }
+    if (any_mma) {
+      if (!tc_wait_phase(&bar_mma, pmma, a.err)) break;
+      mpend = false;
+    }
+    // epilogue: p = U_i o U_j on this half row, the row max, scale, store
+    float p[32];
+    float m = 0.f;
+    {
+      float uj[32];
+      child_cols(cur.xs[0], y0, S, trow + 0 + 32 * h, B[buf][0], kTerm64, 0, 32 * h, p);
+      child_cols(cur.xs[1], y1, S, trow + 64 + 32 * h, B[buf][1], kTerm64, 0, 32 * h, uj);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        p[q] *= uj[q];
+        m = fmaxf(m, fabsf(p[q]));
+      }
+    }
+    xch[h][row] = m;
+    __syncthreads();
+    m = fmaxf(m, xch[1 - h][row]);
+    // an all-zero vector is legitimate for one category (see post_tc_kernel)
+    int e = 0;
+    if (valid) {
+      if (!isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else if (m > 0.f) (void)frexpf(m, &e);
+      e = max(e, -126);  // 2^-e stays finite for a subnormal maximum
+    }
+    E += e;
+    stage_half(stage, row, h, p, ldexpf(1.f, -e));
+    if (valid && h == 0)
+      a.escale[((size_t)(cur.k - a.n_tips) * R + cur.r) * a.escale_stride + c] = E;
+    __syncthreads();
+    coop_store(a.post + ((size_t)(cur.k - a.n_tips) * C * R + cur.r) * 64, (size_t)R * 64,
+               cur.c0, C, stage);
+    tc::fence_before();
+    __syncthreads();  // TMEM, staging, B[buf] and xch are reused next
+    tc::fence_after();
+    if (!more) break;
+    i = inext;
+    buf ^= 1;
+  }
+  if (tid == 0) {  // bounded drain of whatever a timeout left in flight
+    for (int b = 0; b < 2; ++b)
+      if (tpend[b]) (void)mbar_wait(&bar_tma[b], ptma[b]);
+    if (mpend) (void)mbar_wait(&bar_mma, pmma);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------------------
 // Pre-order level (Eq. 4) with the per-category Eq. 8 terms
 // ---------------------------------------------------------------------------
 template <typename T>  // float only
@@ -844,14 +1048,36 @@ __global__ void __launch_bounds__(kTcRows) ratio_tc_kernel(LevelArgs<T> a) {
   }
 }
 
+// Streaming multiprocessors of the current device (queried once per device).
+inline int tc_sm_count() {
+  static int count[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!count[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    count[dev] = n > 0 ? n : 1;
+  }
+  return count[dev];
+}
+
 template <typename T = float>
 inline cudaError_t launch_tc64(const LevelArgs<float>& a, bool post, cudaStream_t st) {
-  if (post) {
-    dim3 grid(a.n_tiles, a.n_level, a.root_level ? 1 : a.n_cat);
+  if (post && a.root_level) {
+    dim3 grid(a.n_tiles, a.n_level, 1);
     return launch_pdl(post_tc_kernel<float>, grid, kTcThreads, kTcPostSmem, st, a);
   }
-  dim3 grid(a.n_tiles, a.n_level, a.n_cat);
-  return launch_pdl(pre_tc_kernel<float>, grid, kTcThreads, kTcPreSmem, st, a);
+  // post-order: persistent, one CTA per SM (shared memory admits no second),
+  // never more CTAs than items
+  const long items = (long)a.n_level * a.n_tiles * a.n_cat;
+  const int grid = (int)(items < tc_sm_count() ? items : tc_sm_count());
+  if (post)
+    return launch_pdl(post_tc_pipe_kernel<float>, dim3(grid), kTcThreads, kTcPipePostSmem, st, a);
+  // pre-order: one CTA per (tile, node, category); a persistent form of it
+  // measured slower (its register pressure spills, and the next item's
+  // [P; dP] tiles can only load once the current item's second MMA is done)
+  dim3 grid3(a.n_tiles, a.n_level, a.n_cat);
+  return launch_pdl(pre_tc_kernel<float>, grid3, kTcThreads, kTcPreSmem, st, a);
 }
 
 template <typename T = float>
@@ -874,6 +1100,9 @@ inline cudaError_t prepare_tc64() {
   cudaError_t e = cudaFuncSetAttribute(post_tc_kernel<float>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kTcPostSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(post_tc_pipe_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcPipePostSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(pre_tc_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)kTcPreSmem);
