@@ -164,6 +164,41 @@ int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out,
 int phylo_forward_device(phylo_ctx* ctx, double* out);
 int phylo_backward_device(phylo_ctx* ctx, double* out);
 
+/* Chain-rule epilogues on the gradient of the most recent evaluation on
+ * this context (phylo_evaluate, phylo_evaluate_device or
+ * phylo_backward_device; PHYLO_ESTATE before the first), for the branch
+ * parameterisations the paper names (Methods: a branch length is the
+ * difference of the parent's and child's node heights in time units times
+ * a possibly branch-specific rate; for a strict clock the branch
+ * derivatives are further reduced over a set of branches).  g_i denotes
+ * d log P(Y)/d t_i, branch i being the branch above node i.
+ *
+ * With on_device = 0 every pointer is host memory and the call
+ * synchronises the stream; with on_device = 1 every pointer is device
+ * memory and the call is asynchronous on the stream (the inputs are read
+ * by the kernels, so they must stay valid until the stream reaches them).
+ * Inputs are validated on the host only in the host form. */
+
+/* t_i = rate_i x time_i (2N-2 of each):
+ *   d_rates[i] = time_i g_i,  d_times[i] = rate_i g_i.
+ * Either output may be NULL. */
+int phylo_gradient_rate_time(phylo_ctx* ctx, const double* rates, const double* times,
+                             double* d_rates, double* d_times, int on_device);
+
+/* t_i = rate_i (h_parent(i) - h_i) for node heights h (2N-1 values, tips
+ * included): d_heights[k] = -rate_k g_k (k not the root)
+ *                          + sum over children c of k of rate_c g_c.
+ * rates may be NULL (all 1). */
+int phylo_gradient_heights(phylo_ctx* ctx, const double* rates, double* d_heights,
+                           int on_device);
+
+/* *out = sum_j weights[j] g_{branches[j]} over n entries (n <= 2N-2;
+ * branches[j] in [0, 2N-2); weights may be NULL for all 1).  A strict
+ * clock t_i = rate x time_i gives d/d rate = this sum with weights time_i
+ * over all branches.  One FP64 value; the sum runs in a fixed order. */
+int phylo_gradient_branch_sum(phylo_ctx* ctx, const int32_t* branches, const double* weights,
+                              int n, double* out, int on_device);
+
 /* Synchronise the stream and report device-side numeric flags raised since
  * the last check (PHYLO_ENUMERIC) or PHYLO_OK. */
 int phylo_check(phylo_ctx* ctx);

@@ -405,3 +405,53 @@ def brute_force_site_likelihoods(parent, t, Q, pi, rates, weights,
                 prod = prod * Pb[xs, grids[:, pos[b]]][:, None]
         total += w * prod.sum(axis=0)
     return total
+
+
+# ---------------------------------------------------------------------------
+# Branch parameterisations (Methods): a branch length is the difference of
+# the parent's and the child's node heights in time units times a (possibly
+# branch-specific) rate; a strict clock reduces the branch derivatives over
+# a set of branches.  Plain chain rule on the gradient g = d log P / d t.
+# ---------------------------------------------------------------------------
+
+
+def lengths_from_heights(parent, heights, rates=None):
+    """t_i = rate_i (h_parent(i) - h_i) for every non-root node i."""
+    parent = np.asarray(parent)
+    n = len(parent)
+    t = np.zeros(n - 1)
+    for i in range(n):
+        if parent[i] >= 0:
+            r = 1.0 if rates is None else rates[i]
+            t[i] = r * (heights[parent[i]] - heights[i])
+    return t
+
+
+def chain_rate_time(g, rates, times):
+    """(d/d rate_i, d/d time_i) of log P for t_i = rate_i time_i."""
+    g = np.asarray(g, dtype=np.float64)
+    return np.asarray(times) * g, np.asarray(rates) * g
+
+
+def chain_heights(parent, g, rates=None):
+    """d log P / d h_k for t_i = rate_i (h_parent(i) - h_i): branch i
+    contributes -rate_i g_i to its child node i and +rate_i g_i to its
+    parent node."""
+    parent = np.asarray(parent)
+    dh = np.zeros(len(parent))
+    for i in range(len(parent)):
+        p = parent[i]
+        if p < 0:
+            continue
+        r = 1.0 if rates is None else rates[i]
+        dh[i] -= r * g[i]
+        dh[p] += r * g[i]
+    return dh
+
+
+def branch_sum(g, branches, weights=None):
+    """sum_j weights_j g[branches_j] (a strict clock over a set of branches)."""
+    g = np.asarray(g, dtype=np.float64)
+    b = np.asarray(branches, dtype=np.int64)
+    w = np.ones(len(b)) if weights is None else np.asarray(weights, dtype=np.float64)
+    return float(np.sum(w * g[b]))

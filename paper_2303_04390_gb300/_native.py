@@ -52,6 +52,9 @@ SIGNATURES = {
                                              ctypes.POINTER(_vp)]),
     "phylo_forward_device": (_c_int, [_vp, _vp]),
     "phylo_backward_device": (_c_int, [_vp, _vp]),
+    "phylo_gradient_rate_time": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_int]),
+    "phylo_gradient_heights": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "phylo_gradient_branch_sum": (_c_int, [_vp, _vp, _vp, _c_int, _vp, _c_int]),
     "phylo_check": (_c_int, [_vp]),
     "phylo_launches_per_evaluation": (_c_int, [_vp]),
     "phylo_level_counts": (_c_int, [_vp, ctypes.POINTER(_c_int),

@@ -203,6 +203,83 @@ class PhyloContext:
             self._ctx, ctypes.c_void_p(out.data_ptr()), arr))
         return out
 
+    # -- chain-rule epilogues on the last evaluation's gradient ------------
+    # Arguments are numpy arrays (host form, synchronous) or CUDA tensors
+    # (device form, asynchronous on the context's stream; outputs are new
+    # tensors on the same device).
+
+    @staticmethod
+    def _on_device(x):
+        return not isinstance(x, np.ndarray) and getattr(x, "is_cuda", False)
+
+    @staticmethod
+    def _vptr(x):
+        if isinstance(x, np.ndarray):
+            return ctypes.c_void_p(x.ctypes.data)
+        return ctypes.c_void_p(x.data_ptr())
+
+    def _f64(self, x, n):
+        if self._on_device(x):
+            import torch
+            t = x.to(torch.float64).contiguous()
+            if t.numel() != n:
+                raise ValueError(f"expected {n} values")
+            return t
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        if a.size != n:
+            raise ValueError(f"expected {n} values")
+        return a
+
+    def _empty_like_input(self, ref, n):
+        if self._on_device(ref):
+            import torch
+            return torch.empty(n, dtype=torch.float64, device=ref.device)
+        return np.zeros(n)
+
+    def gradient_rate_time(self, rates, times):
+        """(d/d rates, d/d times) for t_i = rates_i times_i."""
+        nb = 2 * self.n_tips - 2
+        r, t = self._f64(rates, nb), self._f64(times, nb)
+        dev = self._on_device(r)
+        dr, dt = self._empty_like_input(r, nb), self._empty_like_input(r, nb)
+        self._check(self._lib.phylo_gradient_rate_time(
+            self._ctx, self._vptr(r), self._vptr(t), self._vptr(dr),
+            self._vptr(dt), int(dev)))
+        return dr, dt
+
+    def gradient_heights(self, rates=None):
+        """d/d h for t_i = rates_i (h_parent(i) - h_i); 2N-1 node heights."""
+        nb, nn = 2 * self.n_tips - 2, 2 * self.n_tips - 1
+        r = None if rates is None else self._f64(rates, nb)
+        dev = r is not None and self._on_device(r)
+        if r is None:
+            out = np.zeros(nn)
+        else:
+            out = self._empty_like_input(r, nn)
+        self._check(self._lib.phylo_gradient_heights(
+            self._ctx, None if r is None else self._vptr(r), self._vptr(out),
+            int(dev)))
+        return out
+
+    def gradient_branch_sum(self, branches, weights=None):
+        """sum_j weights_j g_{branches_j} (a strict clock: weights = times)."""
+        dev = self._on_device(branches)
+        if dev:
+            import torch
+            b = branches.to(torch.int32).contiguous()
+            n = b.numel()
+            w = None if weights is None else self._f64(weights, n)
+            out = torch.empty(1, dtype=torch.float64, device=b.device)
+        else:
+            b = np.ascontiguousarray(branches, dtype=np.int32)
+            n = b.size
+            w = None if weights is None else self._f64(weights, n)
+            out = np.zeros(1)
+        self._check(self._lib.phylo_gradient_branch_sum(
+            self._ctx, self._vptr(b), None if w is None else self._vptr(w), n,
+            self._vptr(out), int(dev)))
+        return out if dev else float(out[0])
+
     def check(self):
         self._check(self._lib.phylo_check(self._ctx))
 

@@ -31,4 +31,77 @@ cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st) {
   return launch_pdl(reduce_kernel, dim3(blocks), dim3(256), 0, st, a);
 }
 
+// ---------------------------------------------------------------------------
+// Chain-rule epilogues (branch parameterisations of the paper's Methods):
+// FP64, a few thousand values, one pass each.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) grad_rate_time_kernel(const double* g, int n_br,
+                                                             const double* rates,
+                                                             const double* times,
+                                                             double* d_rates, double* d_times) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_br) return;
+  if (d_rates) d_rates[i] = times[i] * g[i];
+  if (d_times) d_times[i] = rates[i] * g[i];
+}
+
+// d log P / d h_k = -rate_k g_k + sum_{c child of k} rate_c g_c; the root
+// (node 2N-2) has no branch of its own.
+__global__ void __launch_bounds__(256) grad_heights_kernel(const double* g,
+                                                           const int2* children, int n_tips,
+                                                           const double* rates,
+                                                           double* d_heights) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n_nodes = 2 * n_tips - 1, root = n_nodes - 1;
+  if (k >= n_nodes) return;
+  double acc = 0.0;
+  if (k != root) acc = -(rates ? rates[k] : 1.0) * g[k];
+  if (k >= n_tips) {
+    const int2 ch = children[k];
+    acc += (rates ? rates[ch.x] : 1.0) * g[ch.x];
+    acc += (rates ? rates[ch.y] : 1.0) * g[ch.y];
+  }
+  d_heights[k] = acc;
+}
+
+// One block; thread t sums entries t, t + 256, ... then a fixed-order tree.
+__global__ void __launch_bounds__(256) grad_branch_sum_kernel(const double* g,
+                                                              const int* branches,
+                                                              const double* weights, int n,
+                                                              double* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < n; j += 256) acc += (weights ? weights[j] : 1.0) * g[branches[j]];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+cudaError_t launch_grad_rate_time(const double* g, int n_br, const double* rates,
+                                  const double* times, double* d_rates, double* d_times,
+                                  cudaStream_t st) {
+  if (n_br <= 0) return cudaSuccess;
+  grad_rate_time_kernel<<<(n_br + 255) / 256, 256, 0, st>>>(g, n_br, rates, times, d_rates,
+                                                            d_times);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_heights(const double* g, const int2* children, int n_tips,
+                                const double* rates, double* d_heights, cudaStream_t st) {
+  const int n_nodes = 2 * n_tips - 1;
+  grad_heights_kernel<<<(n_nodes + 255) / 256, 256, 0, st>>>(g, children, n_tips, rates,
+                                                             d_heights);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_branch_sum(const double* g, const int* branches, const double* weights,
+                                   int n, double* out, cudaStream_t st) {
+  grad_branch_sum_kernel<<<1, 256, 0, st>>>(g, branches, weights, n, out);
+  return cudaGetLastError();
+}
+
 }  // namespace phylo

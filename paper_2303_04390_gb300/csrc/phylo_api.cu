@@ -42,6 +42,7 @@ struct Layout {
   Region vsplit;  // tensor-core path: eigenvectors as double-float tables
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
   Region gpart, lpart, out;  // out = [logL, grad...] followed by the flag word
+  Region chain_a, chain_b, chain_out, chain_idx;  // chain-rule epilogue staging
   size_t total = 0;
 };
 
@@ -125,6 +126,10 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.gpart, tmp);
   ok &= add_region(L, L.lpart, (size_t)L.n_tiles * 8);
   ok &= add_region(L, L.out, n_nodes * 8 + 8);
+  ok &= add_region(L, L.chain_a, n_nodes * 8);
+  ok &= add_region(L, L.chain_b, n_nodes * 8);
+  ok &= add_region(L, L.chain_out, 2 * n_nodes * 8);
+  ok &= add_region(L, L.chain_idx, n_br * sizeof(int));
   if (!ok) return "size overflow";
   *Lp = L;
   return nullptr;
@@ -146,6 +151,7 @@ struct phylo_ctx {
   cudaGraphExec_t fwd_exec = nullptr;  // matrices + post-order + logL reduction
   cudaGraphExec_t bwd_exec = nullptr;  // pre-order + gradient reduction
   bool forward_valid = false;          // post-order partials match the inputs
+  bool have_grad = false;              // out holds the gradient of an evaluation
   bool graph_dirty = true;
   bool phase_dirty = true;
   bool prepared = false;
@@ -529,6 +535,7 @@ int launch_eval(phylo_ctx* ctx) {
     rc = run_phases(ctx, 0, kPhases - 1, nullptr);
     if (rc) return rc;
     ctx->forward_valid = true;
+    ctx->have_grad = true;
     return PHYLO_OK;
   }
   if (ctx->graph_dirty || !ctx->gexec) {
@@ -537,6 +544,7 @@ int launch_eval(phylo_ctx* ctx) {
   }
   CUDA_TRY(ctx, cudaGraphLaunch(ctx->gexec, ctx->stream), "cudaGraphLaunch");
   ctx->forward_valid = true;
+  ctx->have_grad = true;
   return PHYLO_OK;
 }
 
@@ -728,6 +736,7 @@ int phylo_set_tree(phylo_ctx* ctx, const int32_t* parent) {
   if ((rc = build_schedule(ctx))) return rc;
   invalidate_graph(ctx);
   ctx->have_tree = true;
+  ctx->have_grad = false;  // branch numbering may have changed
   return PHYLO_OK;
 }
 
@@ -1056,11 +1065,125 @@ int phylo_backward_device(phylo_ctx* ctx, double* out) {
   if (ctx->flags & PHYLO_FLAG_NO_GRAPH) rc = run_phases(ctx, 2, 3, nullptr);
   else rc = run_phases(ctx, 2, 3, &ctx->bwd_exec);
   if (rc) return rc;
+  ctx->have_grad = true;
   if (out != ctx->dev<double>(ctx->L.out) + 1)
     CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->dev<double>(ctx->L.out) + 1,
                                   (2 * (size_t)ctx->N - 2) * 8, cudaMemcpyDeviceToDevice,
                                   ctx->stream),
              "copy gradient");
+  return PHYLO_OK;
+}
+
+// ---- chain-rule epilogues ------------------------------------------------
+
+int gradient_ready(phylo_ctx* ctx) {
+  if (!ctx->have_grad)
+    return fail(ctx, PHYLO_ESTATE, "no gradient on this context: evaluate first");
+  return PHYLO_OK;
+}
+
+int phylo_gradient_rate_time(phylo_ctx* ctx, const double* rates, const double* times,
+                             double* d_rates, double* d_times, int on_device) {
+  if (!ctx) return PHYLO_EINVAL;
+  if (!rates || !times) return fail(ctx, PHYLO_EINVAL, "rates and times must not be NULL");
+  int rc = gradient_ready(ctx);
+  if (rc) return rc;
+  const int nb = 2 * ctx->N - 2;
+  const double* g = ctx->dev<double>(ctx->L.out) + 1;
+  if (on_device) {
+    CUDA_TRY(ctx, launch_grad_rate_time(g, nb, rates, times, d_rates, d_times, ctx->stream),
+             "chain-rule kernel");
+    return PHYLO_OK;
+  }
+  for (int i = 0; i < nb; ++i)
+    if (!std::isfinite(rates[i]) || !std::isfinite(times[i]))
+      return fail(ctx, PHYLO_EINVAL, "branch %d: rate and time must be finite", i);
+  if ((rc = upload(ctx, ctx->L.chain_a, rates, nb, "upload rates"))) return rc;
+  if ((rc = upload(ctx, ctx->L.chain_b, times, nb, "upload times"))) return rc;
+  double* out = ctx->dev<double>(ctx->L.chain_out);
+  CUDA_TRY(ctx, launch_grad_rate_time(g, nb, ctx->dev<double>(ctx->L.chain_a),
+                                      ctx->dev<double>(ctx->L.chain_b), out, out + nb,
+                                      ctx->stream),
+           "chain-rule kernel");
+  if (d_rates)
+    CUDA_TRY(ctx, cudaMemcpyAsync(d_rates, out, nb * 8, cudaMemcpyDeviceToHost, ctx->stream),
+             "download");
+  if (d_times)
+    CUDA_TRY(ctx, cudaMemcpyAsync(d_times, out + nb, nb * 8, cudaMemcpyDeviceToHost,
+                                  ctx->stream),
+             "download");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  return PHYLO_OK;
+}
+
+int phylo_gradient_heights(phylo_ctx* ctx, const double* rates, double* d_heights,
+                           int on_device) {
+  if (!ctx) return PHYLO_EINVAL;
+  if (!d_heights) return fail(ctx, PHYLO_EINVAL, "d_heights is NULL");
+  int rc = gradient_ready(ctx);
+  if (rc) return rc;
+  const int nb = 2 * ctx->N - 2, n_nodes = 2 * ctx->N - 1;
+  const double* g = ctx->dev<double>(ctx->L.out) + 1;
+  const int2* children = ctx->dev<int2>(ctx->L.children);
+  if (on_device) {
+    CUDA_TRY(ctx, launch_grad_heights(g, children, ctx->N, rates, d_heights, ctx->stream),
+             "chain-rule kernel");
+    return PHYLO_OK;
+  }
+  const double* rd = nullptr;
+  if (rates) {
+    for (int i = 0; i < nb; ++i)
+      if (!std::isfinite(rates[i]))
+        return fail(ctx, PHYLO_EINVAL, "branch %d: rate must be finite", i);
+    if ((rc = upload(ctx, ctx->L.chain_a, rates, nb, "upload rates"))) return rc;
+    rd = ctx->dev<double>(ctx->L.chain_a);
+  }
+  double* out = ctx->dev<double>(ctx->L.chain_out);
+  CUDA_TRY(ctx, launch_grad_heights(g, children, ctx->N, rd, out, ctx->stream),
+           "chain-rule kernel");
+  CUDA_TRY(ctx, cudaMemcpyAsync(d_heights, out, n_nodes * 8, cudaMemcpyDeviceToHost,
+                                ctx->stream),
+           "download");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  return PHYLO_OK;
+}
+
+int phylo_gradient_branch_sum(phylo_ctx* ctx, const int32_t* branches, const double* weights,
+                              int n, double* out, int on_device) {
+  if (!ctx) return PHYLO_EINVAL;
+  const int nb = 2 * ctx->N - 2;
+  if (!out) return fail(ctx, PHYLO_EINVAL, "out is NULL");
+  if (n < 0 || n > nb) return fail(ctx, PHYLO_EINVAL, "n = %d must be in [0, %d]", n, nb);
+  if (n > 0 && !branches) return fail(ctx, PHYLO_EINVAL, "branches is NULL");
+  int rc = gradient_ready(ctx);
+  if (rc) return rc;
+  const double* g = ctx->dev<double>(ctx->L.out) + 1;
+  if (on_device) {
+    CUDA_TRY(ctx, launch_grad_branch_sum(g, reinterpret_cast<const int*>(branches), weights, n,
+                                         out, ctx->stream),
+             "chain-rule kernel");
+    return PHYLO_OK;
+  }
+  for (int j = 0; j < n; ++j) {
+    if (branches[j] < 0 || branches[j] >= nb)
+      return fail(ctx, PHYLO_EINVAL, "branches[%d] = %d is not a branch", j, branches[j]);
+    if (weights && !std::isfinite(weights[j]))
+      return fail(ctx, PHYLO_EINVAL, "weights[%d] must be finite", j);
+  }
+  const double* wd = nullptr;
+  if (n > 0) {
+    if ((rc = upload(ctx, ctx->L.chain_idx, branches, n, "upload branches"))) return rc;
+    if (weights) {
+      if ((rc = upload(ctx, ctx->L.chain_b, weights, n, "upload weights"))) return rc;
+      wd = ctx->dev<double>(ctx->L.chain_b);
+    }
+  }
+  double* dout = ctx->dev<double>(ctx->L.chain_out);
+  CUDA_TRY(ctx, launch_grad_branch_sum(g, ctx->dev<int>(ctx->L.chain_idx), wd, n, dout,
+                                       ctx->stream),
+           "chain-rule kernel");
+  CUDA_TRY(ctx, cudaMemcpyAsync(out, dout, 8, cudaMemcpyDeviceToHost, ctx->stream), "download");
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   return PHYLO_OK;
 }
 

@@ -193,4 +193,13 @@ template <typename T>
 cudaError_t prepare_kernels(int SP, int RP);
 cudaError_t launch_reduce(const ReduceArgs& a, cudaStream_t st);
 
+// Chain-rule epilogues on the gradient g [2N-2] (kernels_fp64.cu).
+cudaError_t launch_grad_rate_time(const double* g, int n_br, const double* rates,
+                                  const double* times, double* d_rates, double* d_times,
+                                  cudaStream_t st);
+cudaError_t launch_grad_heights(const double* g, const int2* children, int n_tips,
+                                const double* rates, double* d_heights, cudaStream_t st);
+cudaError_t launch_grad_branch_sum(const double* g, const int* branches, const double* weights,
+                                   int n, double* out, cudaStream_t st);
+
 }  // namespace phylo
