@@ -306,11 +306,12 @@ constexpr int kPmatTcThreads = 256;  // one 4 x 4 block of (s, t) per thread
 struct PmatTcSmem {
   float vt_h[64][64], vt_l[64][64];  // V transposed: [m][s]
   float vi_h[64][64], vi_l[64][64];  // Vinv: [m][t]
+  float pi_h[64], pi_l[64];          // root distribution (reversible form)
   DF e[64], d[64];
   uint64_t bar;
 };
-static_assert(sizeof(float) * kEigenSplitFloats == 4 * 64 * 64 * sizeof(float),
-              "eigen table size");
+static_assert(offsetof(PmatTcSmem, e) == kEigenSplitFloats * sizeof(float),
+              "the staged table is the host's eigen split");
 constexpr size_t kPmatTcSmem = sizeof(PmatTcSmem);
 
 template <typename T>  // float only
@@ -351,6 +352,76 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
     }
     return;
   }
+  unsigned char* base = static_cast<unsigned char*>(a.P) + (size_t)unit * kTcUnitBytes;
+  if (a.reversible) {
+    // Vinv[m][t] = pi_t V[t][m]: P - I = K diag(pi) with K = V diag(e) V'
+    // symmetric, so only the 136 blocks (sb <= tb) of the 16 x 16 grid of
+    // 4 x 4 blocks are contracted; each writes itself and its mirror
+    // P[t][s] = pi_s K_st.
+    if (tid >= 136) return;
+    int sb = 0, rem = tid;
+    while (rem >= 16 - sb) {
+      rem -= 16 - sb;
+      ++sb;
+    }
+    const int tb = sb + rem, s0 = 4 * sb, t0 = 4 * tb;
+    DF kP[4][4], kD[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) kP[i][j] = kD[i][j] = DF{0.f, 0.f};
+    for (int m = 0; m < S; ++m) {
+      const float4 sh = *reinterpret_cast<const float4*>(&sm.vt_h[m][s0]);
+      const float4 sl = *reinterpret_cast<const float4*>(&sm.vt_l[m][s0]);
+      const float4 th = *reinterpret_cast<const float4*>(&sm.vt_h[m][t0]);
+      const float4 tl = *reinterpret_cast<const float4*>(&sm.vt_l[m][t0]);
+      const DF em = sm.e[m], dm = sm.d[m];
+      const DF v[4] = {{sh.x, sl.x}, {sh.y, sl.y}, {sh.z, sl.z}, {sh.w, sl.w}};
+      const DF w[4] = {{th.x, tl.x}, {th.y, tl.y}, {th.z, tl.z}, {th.w, tl.w}};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const DF ve = df_mul(v[i], em), vd = df_mul(v[i], dm);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          df_fma(kP[i][j], ve, w[j]);
+          df_fma(kD[i][j], vd, w[j]);
+        }
+      }
+    }
+    float P[4][4], D[4][4], Pm[4][4], Dm[4][4];  // block (sb, tb) and its mirror
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int s = s0 + i, t = t0 + j;
+        const DF pt = {sm.pi_h[t], sm.pi_l[t]}, ps = {sm.pi_h[s], sm.pi_l[s]};
+        P[i][j] = df_round(df_mul(kP[i][j], pt), s == t && s < S);
+        D[i][j] = df_round(df_mul(kD[i][j], pt), false);
+        Pm[j][i] = df_round(df_mul(kP[i][j], ps), s == t && s < S);
+        Dm[j][i] = df_round(df_mul(kD[i][j], ps), false);
+      }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      put_split3_4(base + kUnitPdp, kTerm128, s0 + i, t0,
+                   make_float4(P[i][0], P[i][1], P[i][2], P[i][3]));
+      put_split3_4(base + kUnitPdp, kTerm128, 64 + s0 + i, t0,
+                   make_float4(D[i][0], D[i][1], D[i][2], D[i][3]));
+      put_split3_4(base + kUnitPt, kTerm64, t0 + i, s0,
+                   make_float4(P[0][i], P[1][i], P[2][i], P[3][i]));
+    }
+    if (sb != tb) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        put_split3_4(base + kUnitPdp, kTerm128, t0 + j, s0,
+                     make_float4(Pm[j][0], Pm[j][1], Pm[j][2], Pm[j][3]));
+        put_split3_4(base + kUnitPdp, kTerm128, 64 + t0 + j, s0,
+                     make_float4(Dm[j][0], Dm[j][1], Dm[j][2], Dm[j][3]));
+        put_split3_4(base + kUnitPt, kTerm64, s0 + j, t0,
+                     make_float4(Pm[0][j], Pm[1][j], Pm[2][j], Pm[3][j]));
+      }
+    }
+    return;
+  }
   const int s0 = 4 * (tid / 16), t0 = 4 * (tid % 16);
   DF accP[4][4], accD[4][4];
 #pragma unroll
@@ -375,7 +446,6 @@ __global__ void __launch_bounds__(kPmatTcThreads) pmat_tc_kernel(PmatArgs a) {
       }
     }
   }
-  unsigned char* base = static_cast<unsigned char*>(a.P) + (size_t)unit * kTcUnitBytes;
   float P[4][4], D[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -1091,7 +1161,9 @@ template <typename T = float>
 inline cudaError_t launch_pmat_tc64(const PmatArgs& a, cudaStream_t st) {
   const int units = a.n_branches * a.n_cat;
   if (units <= 0) return cudaSuccess;
-  pmat_tc_kernel<float><<<units, kPmatTcThreads, kPmatTcSmem, st>>>(a);
+  // the reversible form has 136 blocks of (s, t) per unit: 5 warps, so that
+  // three units share an SM
+  pmat_tc_kernel<float><<<units, a.reversible ? 160 : kPmatTcThreads, kPmatTcSmem, st>>>(a);
   return cudaGetLastError();
 }
 

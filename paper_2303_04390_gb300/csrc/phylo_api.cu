@@ -152,6 +152,7 @@ struct phylo_ctx {
   cudaGraphExec_t bwd_exec = nullptr;  // pre-order + gradient reduction
   bool forward_valid = false;          // post-order partials match the inputs
   bool have_grad = false;              // out holds the gradient of an evaluation
+  bool eig_reversible = false;         // V, Vinv are the symmetric decomposition
   bool graph_dirty = true;
   bool phase_dirty = true;
   bool prepared = false;
@@ -269,6 +270,7 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     PmatArgs pa{};
     pa.vsplit = ctx->L.vsplit.bytes ? ctx->dev<float>(ctx->L.vsplit) : nullptr;
+    pa.reversible = ctx->eig_reversible;
     pa.V = ctx->dev<double>(ctx->L.V);
     pa.Vinv = ctx->dev<double>(ctx->L.Vinv);
     pa.lambda = ctx->dev<double>(ctx->L.lambda);
@@ -854,7 +856,7 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
   if ((rc = upload(ctx, ctx->L.Vinv, Vinv, (size_t)S * S, "upload Vinv"))) return rc;
   if (ctx->L.vsplit.bytes) {
     std::vector<float> split(kEigenSplitFloats);
-    build_eigen_split(S, V, Vinv, split.data());
+    ctx->eig_reversible = build_eigen_split(S, V, Vinv, pi, split.data());
     if ((rc = upload(ctx, ctx->L.vsplit, split.data(), split.size(), "upload V split"))) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }

@@ -62,11 +62,18 @@ constexpr int kTcTilePatterns = 128;
 constexpr size_t kTcUnitBytes = 73728;
 
 // The eigenvectors as double-float pairs for the tensor-core path's matrix
-// kernel: out = [V' hi][V' lo][Vinv hi][Vinv lo], each 64 x 64 floats,
-// V' the transpose of V, zero outside S x S.
-constexpr size_t kEigenSplitFloats = 4 * 64 * 64;
-inline void build_eigen_split(int S, const double* V, const double* Vinv, float* out) {
+// kernel: out = [V' hi][V' lo][Vinv hi][Vinv lo] (each 64 x 64 floats, V'
+// the transpose of V, zero outside S x S) then [pi hi][pi lo] (64 each).
+// Returns whether the decomposition is the symmetric one of a reversible
+// model, Vinv[m][t] = pi_t V[t][m] (then P(t) = I + V diag(e) V' diag(pi)
+// and P_st pi_s = P_ts pi_t, which the kernel exploits).
+constexpr size_t kEigenSplitFloats = 4 * 64 * 64 + 2 * 64;
+inline bool build_eigen_split(int S, const double* V, const double* Vinv, const double* pi,
+                              float* out) {
   for (int i = 0; i < (int)kEigenSplitFloats; ++i) out[i] = 0.f;
+  double vmax = 0.0;
+  for (int i = 0; i < S * S; ++i) vmax = Vinv[i] > vmax ? Vinv[i] : (-Vinv[i] > vmax ? -Vinv[i] : vmax);
+  bool reversible = true;
   for (int m = 0; m < S; ++m)
     for (int s = 0; s < S; ++s) {
       const double v = V[s * S + m], w = Vinv[m * S + s];
@@ -75,7 +82,15 @@ inline void build_eigen_split(int S, const double* V, const double* Vinv, float*
       out[1 * 4096 + m * 64 + s] = (float)(v - (double)vh);
       out[2 * 4096 + m * 64 + s] = wh;
       out[3 * 4096 + m * 64 + s] = (float)(w - (double)wh);
+      const double dev = w - pi[s] * v;
+      if (!(dev <= 1e-10 * vmax && -dev <= 1e-10 * vmax)) reversible = false;
     }
+  for (int s = 0; s < S; ++s) {
+    const float ph = (float)pi[s];
+    out[4 * 4096 + s] = ph;
+    out[4 * 4096 + 64 + s] = (float)(pi[s] - (double)ph);
+  }
+  return reversible;
 }
 
 // Exponent planes per node: R on the tensor-core path, else 1 (one
@@ -135,6 +150,7 @@ struct LevelArgs {
 
 struct PmatArgs {
   const float* vsplit;   // tensor-core path: build_eigen_split's table
+  int reversible;        // tensor-core path: the table's decomposition is symmetric
   const double* V;       // [S][S]
   const double* Vinv;    // [S][S]
   const double* lambda;  // [S]

@@ -302,8 +302,9 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   // static storage, not an allocation; the copy completes before this call
   // returns (the stream is synchronised below)
   static thread_local float vsplit[kEigenSplitFloats];
+  bool reversible = false;
   if (L.vsplit.bytes) {
-    build_eigen_split(S, V, Vinv, vsplit);
+    reversible = build_eigen_split(S, V, Vinv, root_freqs, vsplit);
     NA_TRY(up(L.vsplit, vsplit, sizeof(vsplit)), "upload V split");
   }
   NA_TRY(up(L.lambda, lambda, (size_t)S * 8), "upload lambda");
@@ -328,6 +329,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
 
   PmatArgs pa{};
   pa.vsplit = L.vsplit.bytes ? reinterpret_cast<const float*>(ws + L.vsplit.off) : nullptr;
+  pa.reversible = reversible;
   pa.V = reinterpret_cast<const double*>(ws + L.V.off);
   pa.Vinv = reinterpret_cast<const double*>(ws + L.Vinv.off);
   pa.lambda = reinterpret_cast<const double*>(ws + L.lambda.off);

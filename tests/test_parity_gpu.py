@@ -250,3 +250,20 @@ def test_full_size_workloads(name):
         assert abs(grad[a] - grad[b]) <= 2 * max(
             TOL[prec]["g_rel"] * abs(ref[1][a]), TOL[prec]["g_cond"] * ref[3][a])
         ctx.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_general_eigen_form(precision):
+    """Eigenvector columns rescaled: the same P(t), but not the symmetric
+    decomposition of a reversible model, so the matrix build takes its
+    general form (the symmetric one is what set_rate_matrix produces)."""
+    import paper_2303_04390_gb300 as pg
+    w = synth.small_workload(14, 61, 4, 150, seed=77)
+    V, Vi, lam = pg.eigen_reversible(w.Q, w.pi)
+    c = np.random.default_rng(7).uniform(0.5, 2.0, 61)
+    ref = oracle_eval(w)
+    ctx = pg.from_workload(w, precision)
+    ctx.set_eigen(V * c, Vi / c[:, None], lam, w.pi)
+    logL, grad = ctx.evaluate()
+    compare(logL, grad, ref, precision, "general eigen form")
+    ctx.close()
