@@ -383,7 +383,7 @@ constexpr int kDescCompactX = kDescFlagCompact0, kDescCompactY = kDescFlagCompac
 // capping them at 3 blocks (168 registers) measured 12% faster on the
 // 256-taxon amino-acid workload than the unbounded 212 registers (2 blocks).
 template <typename T, int SP>
-constexpr int kSmallMinBlocks = (SP == 20 && sizeof(T) == 4) ? 3 : 1;
+constexpr int kSmallMinBlocks = (SP == 20 && sizeof(T) == 4) ? 3 : 0;
 
 // Post-order level (Eq. 2): p_k = (P_i p_i) o (P_j p_j), rescaled; at the
 // root also log P(Y_c) (Eq. 3) weighted by W_c and summed per tile.
