@@ -275,6 +275,8 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
   __syncthreads();
   T* P = static_cast<T*>(a.P);
   T* dP = static_cast<T*>(a.dP);
+  // FP32 with 4 states: per branch [P' | dP' | P] of every category
+  constexpr bool kP4 = SP == 4 && std::is_same<T, float>::value;
   for (int idx = threadIdx.x; idx < UPB * SP * SP; idx += blockDim.x) {
     const int u = idx / (SP * SP), e = idx % (SP * SP);
     const int unit = unit0 + u;
@@ -289,8 +291,16 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
       }
       if (s == t) acc += 1.0;  // P = I + V diag(e^x - 1) Vinv
     }
-    P[(size_t)unit * SP * SP + e] = (T)acc;
-    dP[(size_t)unit * SP * SP + e] = (T)dacc;
+    if constexpr (kP4) {
+      const int b = unit / R, r = unit % R;
+      T* base = P + (size_t)b * kP4MatKinds * R * 16;
+      base[r * 16 + t * 4 + s] = (T)acc;
+      base[(R + r) * 16 + t * 4 + s] = (T)dacc;
+      base[(2 * R + r) * 16 + e] = (T)acc;
+    } else {
+      P[(size_t)unit * SP * SP + e] = (T)acc;
+      dP[(size_t)unit * SP * SP + e] = (T)dacc;
+    }
   }
 }
 

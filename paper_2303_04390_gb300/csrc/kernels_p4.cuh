@@ -11,9 +11,11 @@
 //    input) before it computes, so each warp keeps 3 x R x 512 bytes in
 //    flight;
 //  - the block's transition matrices are staged in shared memory by 1-D
-//    bulk copies (cp.async.bulk) on an mbarrier, then transposed once per
-//    block so that P v, dP v and P' a all run on the packed FP32 FMA
-//    (__ffma2_rn, two lanes per instruction) from 16-byte broadcast reads;
+//    bulk copies (cp.async.bulk) on an mbarrier, one per child, in the
+//    orientations the products read (the matrix kernel writes P', dP' and
+//    P per branch), so that P v, dP v and P' a all run on the packed FP32
+//    FMA (__ffma2_rn, two lanes per instruction) from 16-byte broadcast
+//    reads;
 //  - the tile's gradient sums are FP32 pairs kept exact with error-free
 //    transformations (converted to FP64 once per tile).
 #pragma once
@@ -64,15 +66,31 @@ __device__ __forceinline__ float max4(float2 lo, float2 hi) {
   return fmaxf(fmaxf(fabsf(lo.x), fabsf(lo.y)), fmaxf(fabsf(hi.x), fabsf(hi.y)));
 }
 
-// Shared layout of one block: for each staged matrix block m (R x 16
-// floats, category-major) a raw copy and its per-category transpose.
-//   m = 0..3:  P_i, P_j, dP_i, dP_j
-//   m = 4..7:  P of the tip branches below a cherry child (i: 4, 5; j: 6, 7)
-template <int NM, int RM>
+// Shared layout of one block.  m[x] holds child x's branch block as the
+// matrix kernel wrote it: P' of every category (R x 16 floats) and, for the
+// pre-order step, dP' and P after it (float4 offsets 0, 4R and 8R).  g holds
+// P' of the tip branches below a cherry child (i: 0, 1; j: 2, 3).
+template <int RM, bool PRE, bool CH>
 struct P4Mats {
-  float4 raw[NM][RM * 4];  // as copied (rows)
-  float4 tr[NM][RM * 4];   // transposes (rows of M' = columns of M)
+  float4 m[2][(PRE ? kP4MatKinds : 1) * RM * 4];
+  float4 g[CH ? 4 : 1][RM * 4];
 };
+
+// Power-of-two rescale of a vector whose largest magnitude is mx (finite,
+// > 0): returns e with mx = f 2^e, f in [0.5, 1) (as frexp), and sets
+// s = 2^-e.  Normal mx reads the exponent field; subnormal or huge mx takes
+// frexpf/ldexpf.
+__device__ __forceinline__ int p4_rescale(float mx, float& s) {
+  const int b = (__float_as_int(mx) >> 23) & 0xff;
+  if (b >= 1 && b <= 252) {
+    s = __int_as_float((253 - b) << 23);
+    return b - 126;
+  }
+  int e;
+  (void)frexpf(mx, &e);
+  s = ldexpf(1.f, -e);
+  return e;
+}
 
 // Cherry fusion.  A cherry is a non-root internal node whose two children
 // are tips with compact states.  It gets no post-order launch and stores no
@@ -115,16 +133,17 @@ __device__ __forceinline__ void p4_child(int y, int S, float4 v,
 // unbounded.
 constexpr int kP4PreMinBlocks = 12;
 
-template <int RM, bool PRE, bool CH>
+// RM: categories unrolled (R <= RM); EX: R == RM, so that no per-category
+// test is left at run time.
+template <int RM, bool EX, bool PRE, bool CH>
 __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     level_p4_kernel(LevelArgs<float> a) {
-  constexpr int NM = CH ? 8 : 4;
-  __shared__ P4Mats<NM, RM> sm;
+  __shared__ P4Mats<RM, PRE, CH> sm;
   __shared__ uint64_t bar;
   __shared__ F2 red[kP4Threads / 32][2];
   __shared__ double lred[kP4Threads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int R = EX ? RM : a.n_cat, C = a.n_patterns, S = a.n_states;
   const int4 d = a.level_desc[blockIdx.y];
   const int k = d.x, bi = d.y, bj = d.z;
   const bool ci = d.w & kDescFlagCompact0, cj = d.w & kDescFlagCompact1;
@@ -133,25 +152,23 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
   const int2 gj2 = hj_ ? a.children[bj] : make_int2(0, 0);
   const int c = blockIdx.x * kP4Threads + tid;
   const bool valid = c < C;
-  const uint32_t mbytes = (uint32_t)R * 64;
+  const uint32_t mbytes = (uint32_t)R * 64;  // one matrix of every category
+  const uint32_t cbytes = (PRE ? kP4MatKinds : 1) * mbytes;  // a child's block
+  const size_t bstride = (size_t)kP4MatKinds * R * 16;      // floats per branch
   if (tid == 0) mbar_init_fenced(&bar, 1);
   __syncthreads();
   pdl_wait_and_release();
   if (tid == 0) {
     const int n_ch = (int)hi_ + (int)hj_;
-    mbar_expect_tx(&bar, mbytes * ((PRE ? 4 : 2) + 2 * n_ch));
-    bulk_g2s(sm.raw[0], a.P + (size_t)bi * R * 16, mbytes, &bar);
-    bulk_g2s(sm.raw[1], a.P + (size_t)bj * R * 16, mbytes, &bar);
-    if (PRE) {
-      bulk_g2s(sm.raw[2], a.dP + (size_t)bi * R * 16, mbytes, &bar);
-      bulk_g2s(sm.raw[3], a.dP + (size_t)bj * R * 16, mbytes, &bar);
-    }
+    mbar_expect_tx(&bar, 2 * cbytes + 2 * n_ch * mbytes);
+    bulk_g2s(sm.m[0], a.P + (size_t)bi * bstride, cbytes, &bar);
+    bulk_g2s(sm.m[1], a.P + (size_t)bj * bstride, cbytes, &bar);
     if constexpr (CH) {
       for (int x = 0; x < 2; ++x) {
         if (!(x == 0 ? hi_ : hj_)) continue;
         const int2 g = x == 0 ? gi2 : gj2;
-        bulk_g2s(sm.raw[4 + 2 * x], a.P + (size_t)g.x * R * 16, mbytes, &bar);
-        bulk_g2s(sm.raw[5 + 2 * x], a.P + (size_t)g.y * R * 16, mbytes, &bar);
+        bulk_g2s(sm.g[2 * x], a.P + (size_t)g.x * bstride, mbytes, &bar);
+        bulk_g2s(sm.g[2 * x + 1], a.P + (size_t)g.y * bstride, mbytes, &bar);
       }
     }
   }
@@ -188,39 +205,39 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       q[r] = __ldg(reinterpret_cast<const float4*>(a.pre) +
                    ((size_t)(k - a.n_tips) * C + c) * R + r);
   }
+  if (PRE && k == a.root) {  // Eq. 4 at the root: q = pi
+    const float4 pr = make_float4(a.root_pit[0], S > 1 ? a.root_pit[1] : 0.f,
+                                  S > 2 ? a.root_pit[2] : 0.f, S > 3 ? a.root_pit[3] : 0.f);
+#pragma unroll
+    for (int r = 0; r < RM; ++r) q[r] = pr;
+  }
   if (!PRE && valid) {  // a cherry's exponent is 0 (its partials are not rescaled)
     if (bi >= a.n_tips && !hi_) ei = a.escale[(size_t)(bi - a.n_tips) * a.escale_stride + c];
     if (bj >= a.n_tips && !hj_) ej = a.escale[(size_t)(bj - a.n_tips) * a.escale_stride + c];
   }
-  // ---- matrices: wait for the bulk copies, transpose once per block ------
+  // ---- matrices: wait for the bulk copies ---------------------------------
   if (!__syncthreads_and(mbar_wait(&bar, 0))) {
     if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
     return;
   }
-  {
-    const float* raw = reinterpret_cast<const float*>(sm.raw);
-    float* tr = reinterpret_cast<float*>(sm.tr);
-    const int nm = PRE ? 4 : 2, n = (nm + (hi_ || hj_ ? 4 : 0)) * RM * 16;
-    for (int i = tid; i < n; i += kP4Threads) {
-      int m = i / (RM * 16);
-      const int rem = i % (RM * 16), rr = rem / 16, e = rem % 16;
-      if (m >= nm) m += 4 - nm;  // the grandchildren's blocks sit at 4..7
-      const int s = e / 4, t = e % 4;  // tr[m][rr][t][s] = raw[m][rr][s][t]
-      tr[(m * RM + rr) * 16 + t * 4 + s] = raw[(m * RM + rr) * 16 + s * 4 + t];
-    }
-  }
-  __syncthreads();
+  // child x's P', dP' and P of category r
+  const float4* PTi = sm.m[0];
+  const float4* PTj = sm.m[1];
+  const float4* DTi = sm.m[0] + 4 * R;
+  const float4* DTj = sm.m[1] + 4 * R;
+  const float4* Pi = sm.m[0] + 8 * R;
+  const float4* Pj = sm.m[1] + 8 * R;
   if constexpr (CH) {
     // a cherry child's partials from its two tip states
 #pragma unroll
     for (int r = 0; r < RM; ++r) {
       if (!(valid && r < R)) continue;
       if (hi_) {
-        const float4 u = p4_col(sm.tr[4] + r * 4, ya[0], S), w = p4_col(sm.tr[5] + r * 4, yb[0], S);
+        const float4 u = p4_col(sm.g[0] + r * 4, ya[0], S), w = p4_col(sm.g[1] + r * 4, yb[0], S);
         vi[r] = make_float4(u.x * w.x, u.y * w.y, u.z * w.z, u.w * w.w);
       }
       if (hj_) {
-        const float4 u = p4_col(sm.tr[6] + r * 4, ya[1], S), w = p4_col(sm.tr[7] + r * 4, yb[1], S);
+        const float4 u = p4_col(sm.g[2] + r * 4, ya[1], S), w = p4_col(sm.g[3] + r * 4, yb[1], S);
         vj[r] = make_float4(u.x * w.x, u.y * w.y, u.z * w.z, u.w * w.w);
       }
     }
@@ -234,19 +251,19 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       plo[r] = make_float2(0.f, 0.f); phi[r] = plo[r];
       if (r < R) {
         float2 ilo, ihi, jlo, jhi, d0, d1;
-        p4_child<false>(yi, S, vi[r], sm.tr[0] + r * 4, nullptr, ilo, ihi, d0, d1);
-        p4_child<false>(yj, S, vj[r], sm.tr[1] + r * 4, nullptr, jlo, jhi, d0, d1);
+        p4_child<false>(yi, S, vi[r], PTi + r * 4, nullptr, ilo, ihi, d0, d1);
+        p4_child<false>(yj, S, vj[r], PTj + r * 4, nullptr, jlo, jhi, d0, d1);
         plo[r] = __fmul2_rn(ilo, jlo);
         phi[r] = __fmul2_rn(ihi, jhi);
         m = fmaxf(m, max4(plo[r], phi[r]));
       }
     }
     int e = 0;
+    float f = 1.f;
     if (valid) {
       if (!(m > 0.f) || !isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
-      else (void)frexpf(m, &e);
+      else e = p4_rescale(m, f);
     }
-    const float f = ldexpf(1.f, -e);
     e += ei + ej;
     if (k != a.root) {
       if (valid) {
@@ -286,11 +303,6 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     return;
   }
   // ---- Eq. 4 and Eq. 8: children's pre-order partials and the ratio ------
-  float2 rootlo = make_float2(0.f, 0.f), roothi = rootlo;
-  if (k == a.root) {
-    rootlo = make_float2(a.root_pit[0], S > 1 ? a.root_pit[1] : 0.f);
-    roothi = make_float2(S > 2 ? a.root_pit[2] : 0.f, S > 3 ? a.root_pit[3] : 0.f);
-  }
   const bool int_i = bi >= a.n_tips, int_j = bj >= a.n_tips;
   float2 qilo[RM], qihi[RM], qjlo[RM], qjhi[RM];
   float Ni = 0.f, Nj = 0.f, Dn = 0.f, mi = 0.f, mj = 0.f;
@@ -298,11 +310,10 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
   for (int r = 0; r < RM; ++r) {
     qilo[r] = make_float2(0.f, 0.f); qihi[r] = qilo[r]; qjlo[r] = qilo[r]; qjhi[r] = qilo[r];
     if (r < R) {
-      const float2 ql = k == a.root ? rootlo : lo2(q[r]);
-      const float2 qh = k == a.root ? roothi : hi2(q[r]);
+      const float2 ql = lo2(q[r]), qh = hi2(q[r]);
       float2 uilo, uihi, wilo, wihi, ujlo, ujhi, wjlo, wjhi;
-      p4_child<true>(yi, S, vi[r], sm.tr[0] + r * 4, sm.tr[2] + r * 4, uilo, uihi, wilo, wihi);
-      p4_child<true>(yj, S, vj[r], sm.tr[1] + r * 4, sm.tr[3] + r * 4, ujlo, ujhi, wjlo, wjhi);
+      p4_child<true>(yi, S, vi[r], PTi + r * 4, DTi + r * 4, uilo, uihi, wilo, wihi);
+      p4_child<true>(yj, S, vj[r], PTj + r * 4, DTj + r * 4, ujlo, ujhi, wjlo, wjhi);
       const float2 ailo = __fmul2_rn(ql, ujlo), aihi = __fmul2_rn(qh, ujhi);  // a_i
       const float2 ajlo = __fmul2_rn(ql, uilo), ajhi = __fmul2_rn(qh, uihi);  // a_j
       const float w = a.cat_wt[r];
@@ -310,11 +321,11 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       Nj = fmaf(w, dot22(ajlo, ajhi, wjlo, wjhi), Nj);
       Dn = fmaf(w, dot22(ailo, aihi, uilo, uihi), Dn);
       if (int_i) {
-        mtv4r(sm.raw[0] + r * 4, ailo, aihi, qilo[r], qihi[r]);
+        mtv4r(Pi + r * 4, ailo, aihi, qilo[r], qihi[r]);
         mi = fmaxf(mi, max4(qilo[r], qihi[r]));
       }
       if (int_j) {
-        mtv4r(sm.raw[1] + r * 4, ajlo, ajhi, qjlo[r], qjhi[r]);
+        mtv4r(Pj + r * 4, ajlo, ajhi, qjlo[r], qjhi[r]);
         mj = fmaxf(mj, max4(qjlo[r], qjhi[r]));
       }
     }
@@ -324,15 +335,14 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     if (!(Dn > 0.f) || !isfinite(Dn)) {
       atomicOr(a.err, ERR_BAD_RATIO);
     } else {
-      const float W = a.pattern_wt[c];
-      gi = Acc<float>::prod(W, Ni / Dn);
-      gj = Acc<float>::prod(W, Nj / Dn);
+      const float W = a.pattern_wt[c], rd = __fdividef(1.f, Dn);  // Dn << 2^126
+      gi = Acc<float>::prod(W, Ni * rd);
+      gj = Acc<float>::prod(W, Nj * rd);
     }
     if (int_i) {
-      int e = 0;
+      float f = 1.f;
       if (!(mi > 0.f) || !isfinite(mi)) atomicOr(a.err, ERR_ZERO_PARTIAL);
-      else (void)frexpf(mi, &e);
-      const float f = ldexpf(1.f, -e);
+      else (void)p4_rescale(mi, f);
       float4* out = reinterpret_cast<float4*>(a.pre) + ((size_t)(bi - a.n_tips) * C + c) * R;
 #pragma unroll
       for (int r = 0; r < RM; ++r)
@@ -343,10 +353,9 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
         }
     }
     if (int_j) {
-      int e = 0;
+      float f = 1.f;
       if (!(mj > 0.f) || !isfinite(mj)) atomicOr(a.err, ERR_ZERO_PARTIAL);
-      else (void)frexpf(mj, &e);
-      const float f = ldexpf(1.f, -e);
+      else (void)p4_rescale(mj, f);
       float4* out = reinterpret_cast<float4*>(a.pre) + ((size_t)(bj - a.n_tips) * C + c) * R;
 #pragma unroll
       for (int r = 0; r < RM; ++r)
@@ -357,14 +366,24 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
         }
     }
   }
+  // Both children's tile sums in one butterfly: after the first exchange
+  // lanes 0-15 carry child i's pairs and lanes 16-31 child j's, so each
+  // later level moves and adds one pair instead of two.
+  {
+    const bool upper = lane >= 16;
+    F2 mine = upper ? gj : gi;
+    const F2 other = upper ? gi : gj;
+    mine = f2_add(mine, F2{__shfl_xor_sync(kFull, other.hi, 16),
+                           __shfl_xor_sync(kFull, other.lo, 16)});
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    gi = f2_add(gi, Acc<float>::shfl_down(gi, o));
-    gj = f2_add(gj, Acc<float>::shfl_down(gj, o));
+    for (int o = 8; o > 0; o >>= 1) mine = f2_add(mine, Acc<float>::shfl_down(mine, o));
+    if (lane == 0) red[warp][0] = mine;
+    if (lane == 16) red[warp][1] = mine;
   }
-  if (lane == 0) { red[warp][0] = gi; red[warp][1] = gj; }
   __syncthreads();
   if (tid == 0) {
+    gi = red[0][0];
+    gj = red[0][1];
     for (int w = 1; w < kP4Threads / 32; ++w) {
       gi = f2_add(gi, red[w][0]);
       gj = f2_add(gj, red[w][1]);
@@ -374,15 +393,22 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
   }
 }
 
-template <int RM>
-cudaError_t launch_p4(const LevelArgs<float>& a, bool post, cudaStream_t st) {
+template <int RM, bool EX>
+cudaError_t launch_p4_ex(const LevelArgs<float>& a, bool post, cudaStream_t st) {
   dim3 grid(a.n_tiles, a.n_level);
   if (a.level_cherry) {
-    if (post) return launch_pdl(level_p4_kernel<RM, false, true>, grid, kP4Threads, 0, st, a);
-    return launch_pdl(level_p4_kernel<RM, true, true>, grid, kP4Threads, 0, st, a);
+    if (post) return launch_pdl(level_p4_kernel<RM, EX, false, true>, grid, kP4Threads, 0, st, a);
+    return launch_pdl(level_p4_kernel<RM, EX, true, true>, grid, kP4Threads, 0, st, a);
   }
-  if (post) return launch_pdl(level_p4_kernel<RM, false, false>, grid, kP4Threads, 0, st, a);
-  return launch_pdl(level_p4_kernel<RM, true, false>, grid, kP4Threads, 0, st, a);
+  if (post) return launch_pdl(level_p4_kernel<RM, EX, false, false>, grid, kP4Threads, 0, st, a);
+  return launch_pdl(level_p4_kernel<RM, EX, true, false>, grid, kP4Threads, 0, st, a);
+}
+
+template <int RM>
+cudaError_t launch_p4(const LevelArgs<float>& a, bool post, cudaStream_t st) {
+  if (a.n_cat == RM) return launch_p4_ex<RM, true>(a, post, st);
+  if constexpr (RM > 2) return launch_p4_ex<RM, false>(a, post, st);
+  return cudaErrorInvalidValue;
 }
 
 // RP (next power of two >= R) selects the unrolled category count.

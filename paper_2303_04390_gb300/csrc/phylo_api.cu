@@ -78,8 +78,10 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   const size_t n_int = (size_t)N - 1;
   size_t mat, part, tmp, tmp2;
   const bool tc = uses_tensor_cores(L.SP, prec == PHYLO_FP64);
-  if (!mul_ok(n_br * R, tc ? kTcUnitBytes : (size_t)L.SP * L.SP * L.elem, &mat))
-    return "size overflow";
+  const bool p4 = uses_p4_layout(L.SP, prec == PHYLO_FP64);
+  const size_t unit = tc ? kTcUnitBytes
+                         : (size_t)L.SP * L.SP * L.elem * (p4 ? kP4MatKinds : 1);
+  if (!mul_ok(n_br * R, unit, &mat)) return "size overflow";
   if (!mul_ok(n_int, (size_t)C, &tmp) || !mul_ok(tmp, (size_t)R * L.SP * L.elem, &part))
     return "size overflow";
   bool ok = true;
@@ -89,7 +91,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.post_desc, n_int * sizeof(int4));
   ok &= add_region(L, L.pre_desc, n_int * sizeof(int4));
   ok &= add_region(L, L.P, mat);
-  ok &= add_region(L, L.dP, tc ? 0 : mat);  // the tensor-core tiles hold dP
+  ok &= add_region(L, L.dP, tc || p4 ? 0 : mat);  // else the P region holds dP
   ok &= add_region(L, L.post, part);
   ok &= add_region(L, L.pre, part);
   if (C > (1 << 30)) return "n_patterns too large";

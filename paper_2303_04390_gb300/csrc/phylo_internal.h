@@ -52,6 +52,12 @@ constexpr int kWidePatternsF64 = 8;
 #define PHYLO_P4_TILE 64
 #endif
 constexpr int kP4TilePatterns = PHYLO_P4_TILE;
+// Their matrices are built in the orientations the products read, so no
+// kernel transposes them: per branch, [P' of every category][dP' of every
+// category][P of every category] (16 floats each; P' rows are the columns of
+// P).  The dP region is then empty.
+inline bool uses_p4_layout(int SP, bool fp64) { return SP == 4 && !fp64; }
+constexpr int kP4MatKinds = 3;
 
 // FP32 with 21..64 states runs on the tensor cores (kernels_tc64.cuh):
 // 128-pattern tiles and one rescale exponent per (node, category, pattern).
@@ -120,9 +126,11 @@ struct LevelArgs {
   int level_cherry;            // 1 if a node of the level has a fused cherry child
   int n_tips, n_patterns, n_states, n_cat, root;
   const T* P;                  // [2N-2][R][SP][SP], row = parent state
-                               // (tensor-core path: [2N-2][R] operand tiles)
+                               // (tensor-core path: [2N-2][R] operand tiles;
+                               // FP32 4 states: [2N-2][P' | dP' | P][R][16])
   const T* dP;                 // same layout: dP/dt = gamma_r Q P (null on
-                               // the tensor-core path, whose tiles hold dP)
+                               // the tensor-core and FP32 4-state paths,
+                               // whose P region holds dP)
   T* post;                     // [N-1][C][R][SP] post-order partials
   T* pre;                      // [N-1][C][R][SP] pre-order partials
   int* escale;                 // [N-1][planes][escale_stride] cumulative

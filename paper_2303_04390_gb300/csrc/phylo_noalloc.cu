@@ -79,7 +79,9 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   L.n_tiles = (C + ct - 1) / ct;
   const size_t n_nodes = 2 * (size_t)N - 1, n_br = 2 * (size_t)N - 2, n_int = (size_t)N - 1;
   const bool tc = uses_tensor_cores(L.SP, false);
-  const size_t mat = n_br * R * (tc ? kTcUnitBytes : L.SP * L.SP * sizeof(float));
+  const bool p4 = uses_p4_layout(L.SP, false);
+  const size_t mat = n_br * R * (tc ? kTcUnitBytes
+                                    : L.SP * L.SP * sizeof(float) * (p4 ? kP4MatKinds : 1));
   const size_t part = n_int * (size_t)C * R * L.SP * sizeof(float);
   na_add(L, L.children, n_nodes * sizeof(int2));
   na_add(L, L.post_nodes, n_int * sizeof(int));
@@ -87,7 +89,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.post_desc, n_int * sizeof(int4));
   na_add(L, L.pre_desc, n_int * sizeof(int4));
   na_add(L, L.P, mat);
-  na_add(L, L.dP, tc ? 0 : mat);  // the tensor-core tiles hold dP
+  na_add(L, L.dP, tc || p4 ? 0 : mat);  // else the P region holds dP
   na_add(L, L.post, part);
   na_add(L, L.pre, part);
   const size_t eplane = n_int * (size_t)round_up(C, 4) * sizeof(int);
