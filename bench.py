@@ -78,6 +78,16 @@ def algorithmic_bytes(w, precision):
     }
 
 
+def algorithmic_flops(w):
+    """Dense contractions the method needs per evaluation (2 S^2 flops per
+    matrix-vector product of one pattern and category): a tip child's
+    product is a column lookup, so only internal non-root nodes count --
+    post-order P p once (by the parent), pre-order P p, dP p and P' a."""
+    N, C, S, R = w.n_tips, w.n_patterns, w.n_states, w.n_categories
+    unit = 2 * S * S * R * C * (N - 2)
+    return {"pmat": 0, "post": unit, "pre": 3 * unit, "reduce": 0}
+
+
 # ---------------------------------------------------------------------------
 # Clock sampling during the timed regions
 # ---------------------------------------------------------------------------
@@ -237,9 +247,9 @@ def run_reference(args):
 # Our arm
 # ---------------------------------------------------------------------------
 
-def _traffic_record(kernel_phase, workload, precision):
-    """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
+def _profile_record(kernel_phase, workload, precision):
+    """The '- key: value' lines of the committed ncu summary of a phase's
+    kernel, if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles",
                         f"{kernel_phase}_{workload}_{precision}.md")
     if not os.path.exists(path):
@@ -251,9 +261,15 @@ def _traffic_record(kernel_phase, workload, precision):
             rec[k.strip()] = v.strip()
     if rec.get("kernel_source_sha256") != kernel_source_hash():
         return None
+    return rec
+
+
+def _traffic_record(kernel_phase, workload, precision):
+    """dram bytes per launch from the committed ncu summary (or None)."""
+    rec = _profile_record(kernel_phase, workload, precision)
     try:
         return float(rec["dram_bytes_per_launch"]), int(rec["launches"])
-    except (KeyError, ValueError):
+    except (KeyError, ValueError, TypeError):
         return None
 
 
@@ -458,6 +474,10 @@ def run_ours(args):
     kernels = {"pmat": "pmat_kernel", "post": "post-order level kernel",
                "pre": "pre-order level kernel (fused gradient)",
                "reduce": "reduce_kernel"}
+    if precision == "fp32" and w.n_states > 20:
+        kernels = {"pmat": "pmat_tc_kernel", "post": "post_tc_pipe_kernel",
+                   "pre": "pre_tc_kernel + ratio_tc_kernel",
+                   "reduce": "reduce_kernel"}
     phases = {}
     for n_, ms_ in zip(names, phase_ms):
         phases[n_] = {"ms": ms_, "algorithmic_bytes": by[n_],
@@ -480,6 +500,26 @@ def run_ours(args):
         "launches_per_evaluation": n_launch_dom,
         "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
     }
+    tensor = None
+    if precision == "fp32" and w.n_states > 20:
+        # the tensor-core path: algorithmic FLOP rate of its dominant phase
+        # against the sustained BF16 peak (its contractions run on BF16
+        # terms), and the tensor-pipe share ncu measured for that kernel
+        fl = algorithmic_flops(w)
+        tpeak = peaks.get("bf16_tflops_sustained")
+        tkind = "measured" if tpeak else "fallback"
+        tpeak = tpeak or 1700.0
+        tach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
+        rec = _profile_record(dom, args.workload, precision) or {}
+        tensor = {
+            "bound": "tensor", "kernel": kernels[dom], "achieved": tach,
+            "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
+            "peak_kind": f"{tkind} (BF16 dense, sustained)",
+            "algorithmic_flops_per_launch": fl[dom] / n_launch_dom,
+            "tensor_pipe_active_pct_ncu": (float(rec["tensor_pipe_active_pct"])
+                                           if "tensor_pipe_active_pct" in rec
+                                           else None),
+        }
     served = None
     if not args.skip_serve:
         served = run_served(args)
@@ -510,6 +550,7 @@ def run_ours(args):
         "gpu_launches": K * launches,
         "launches_per_step": launches,
         "roofline": roofline,
+        "tensor_roofline": tensor,
         "phases": phases,
         "hbm_gbs_all_phases": sum(by.values()) / (ms / K / 1e3) / 1e9,
         "fp64_path": fp64,
