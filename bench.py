@@ -52,6 +52,7 @@ def _workloads():
         "codon-128": (synth.workload_codon_128, "fp32"),
         "aa-256": (synth.workload_aa_256, "fp32"),
         "jc69-8": (synth.workload_jc69_8, "fp64"),
+        "mmm-122": (synth.workload_mmm_122, "fp32"),
     }
 
 
@@ -474,7 +475,7 @@ def run_ours(args):
     kernels = {"pmat": "pmat_kernel", "post": "post-order level kernel",
                "pre": "pre-order level kernel (fused gradient)",
                "reduce": "reduce_kernel"}
-    if precision == "fp32" and w.n_states > 20:
+    if precision == "fp32" and 20 < w.n_states <= 64:
         kernels = {"pmat": "pmat_tc_kernel", "post": "post_tc_pipe_kernel",
                    "pre": "pre_tc_kernel + ratio_tc_kernel",
                    "reduce": "reduce_kernel"}
@@ -501,7 +502,7 @@ def run_ours(args):
         "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
     }
     tensor = None
-    if precision == "fp32" and w.n_states > 20:
+    if precision == "fp32" and 20 < w.n_states <= 64:
         # the tensor-core path: algorithmic FLOP rate of its dominant phase
         # against the sustained BF16 peak (its contractions run on BF16
         # terms), and the tensor-pipe share ncu measured for that kernel
@@ -569,7 +570,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hky-1024",
-                    choices=["hky-1024", "codon-128", "aa-256", "jc69-8"])
+                    choices=["hky-1024", "codon-128", "aa-256", "jc69-8", "mmm-122"])
     ap.add_argument("--precision", default=None, choices=[None, "fp32", "fp64"])
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")

@@ -962,6 +962,7 @@ inline size_t wide_pre_smem(int R) {
 
 }  // namespace phylo
 
+#include "kernels_big.cuh"
 #include "kernels_p4.cuh"
 #include "kernels_tc64.cuh"
 
@@ -1050,6 +1051,8 @@ cudaError_t launch_level_impl(const LevelArgs<T>& a, int SP, int RP, bool post,
         return launch_pdl(pre_wide_kernel<T>, grid, kWideThreads, wide_pre_smem<T>(a.n_cat), st,
                           a);
       }
+    case 128: return launch_big<T, 128>(a, post, st);
+    case 256: return launch_big<T, 256>(a, post, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1071,6 +1074,8 @@ cudaError_t prepare_impl(int SP, int RP) {
                                   (int)wide_pre_smem<T>(8));
     }
   }
+  if (SP == 128) return prepare_big<T, 128>();
+  if (SP == 256) return prepare_big<T, 256>();
   return cudaSuccess;
 }
 
@@ -1089,6 +1094,8 @@ cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
       if constexpr (std::is_same<T, float>::value) return launch_pmat_tc64(a, st);
       else pmat_kernel<T, 64><<<units, 256, 0, st>>>(a);
       break;
+    case 128: pmat_kernel<T, 128><<<units, 256, 0, st>>>(a); break;
+    case 256: pmat_kernel<T, 256><<<units, 256, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -1,0 +1,422 @@
+// Level kernels for 65..256 states (S_pad 128 or 256), FP64 and FP32, on the
+// CUDA cores: Eq. 2 (with Eq. 3 at the root) and Eq. 4 with the Eq. 8 ratio
+// fused, as in the other level kernels, for state spaces whose transition
+// matrices do not fit in shared memory -- the paper's 122-state
+// Markov-modulated codon model (Results) and 256-state models (Discussion).
+//
+// A block takes a tile of CT patterns of one node and loops over the rate
+// categories.  Thread (g, s) owns state s of the patterns g*CPG .. g*CPG +
+// CPG - 1 (G = 256 / S_pad groups of S_pad threads).  A matrix-vector
+// product streams the matrix through shared memory in chunks:
+//   u = M v   (Eq. 2, and P p, dP p of Eq. 8): chunks of KC columns, thread
+//             s reads row s of the chunk, the patterns' vector chunks are
+//             staged beside it and read as broadcasts;
+//   q = M' a  (Eq. 4): chunks of KC rows, thread t reads column t, a is read
+//             from shared memory as a broadcast.
+// Rescaling follows the other kernels: one power of two per (node, pattern)
+// shared by every category and state; the unscaled values are stored first
+// and scaled in place once the block knows the pattern's maximum (each
+// thread rescales only what it wrote).
+#pragma once
+
+namespace phylo {
+
+constexpr int kBigThreads = 256;
+template <typename T> struct BigCfg;
+template <> struct BigCfg<float> {
+  static constexpr int CT = kBigPatternsF32, KC = 32;
+};
+template <> struct BigCfg<double> {
+  static constexpr int CT = kBigPatternsF64, KC = 16;
+};
+
+// Shared-memory plan of one block (element counts of T).
+template <typename T, int SP>
+struct BigPlan {
+  static constexpr int CT = BigCfg<T>::CT, KC = BigCfg<T>::KC;
+  static constexpr int G = kBigThreads / SP, CPG = CT / G;
+  static constexpr int KP = KC + 16 / (int)sizeof(T);  // 144-byte rows: no bank conflicts
+  static constexpr int WPG = SP / 32;                   // warps per group
+  static constexpr size_t mat = 2 * (size_t)SP * KP;    // two row-chunks (M, dM)
+  static constexpr size_t vec = (size_t)CT * KC;        // the patterns' vector chunk
+  static constexpr size_t uw = 2 * (size_t)CT * SP;     // U, W (pre-order)
+  static constexpr size_t red = (size_t)CT * WPG * 3;   // per-pattern partial sums
+  static size_t bytes(bool pre) { return (mat + vec + (pre ? uw : 0) + red) * sizeof(T); }
+  static_assert((size_t)KC * SP <= mat, "column chunk fits in the row-chunk buffer");
+  static_assert(CT % G == 0 && SP % 32 == 0, "tile shape");
+};
+
+template <typename T, typename V> struct BigVec;
+template <> struct BigVec<float, float> { using type = float4; static constexpr int n = 4; };
+template <> struct BigVec<double, double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float big_dot(float4 a, float4 b, float acc) {
+  acc = fmaf(a.x, b.x, acc);
+  acc = fmaf(a.y, b.y, acc);
+  acc = fmaf(a.z, b.z, acc);
+  return fmaf(a.w, b.w, acc);
+}
+__device__ __forceinline__ double big_dot(double2 a, double2 b, double acc) {
+  acc = fma(a.x, b.x, acc);
+  return fma(a.y, b.y, acc);
+}
+
+// One child's vectors for category r: where they come from.
+template <typename T>
+struct BigChild {
+  int b;            // node
+  bool compact;     // tip with compact states (column lookups)
+  const T* src;     // else: pattern c0's vector; pattern j at src + j * stride
+  size_t stride;
+};
+
+template <typename T>
+__device__ __forceinline__ BigChild<T> big_child(const LevelArgs<T>& a, int b, int c0, int r,
+                                                 int SP) {
+  BigChild<T> x;
+  x.b = b;
+  x.compact = b < a.n_tips && !(a.tip_has_partials && a.tip_has_partials[b]);
+  if (b < a.n_tips) {
+    x.src = a.tip_partials + (size_t)b * a.n_patterns * SP + (size_t)c0 * SP;
+    x.stride = SP;
+  } else {
+    x.src = a.post + (((size_t)(b - a.n_tips) * a.n_patterns + c0) * a.n_cat + r) * SP;
+    x.stride = (size_t)a.n_cat * SP;
+  }
+  return x;
+}
+
+// u[jj] = (M v_j)[s] and, with dM, w[jj] = (dM v_j)[s] for the thread's
+// patterns j = g*CPG + jj.  M, dM: global [SP][SP] (padded rows/columns 0).
+// Every thread of the block calls this (it synchronises).
+template <typename T, int SP, bool WITH_D>
+__device__ __forceinline__ void big_row_mv(const LevelArgs<T>& a, const BigChild<T>& x, const T* __restrict__ M,
+                           const T* __restrict__ dM, int c0, int nvalid, T* smat, T* svec,
+                           int g, int s, T (&u)[BigPlan<T, SP>::CPG],
+                           T (&w)[BigPlan<T, SP>::CPG]) {
+  using PL = BigPlan<T, SP>;
+  constexpr int CPG = PL::CPG, KC = PL::KC, KP = PL::KP, CT = PL::CT;
+  using V = typename BigVec<T, T>::type;
+  constexpr int VN = BigVec<T, T>::n;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) { u[jj] = T(0); w[jj] = T(0); }
+  if (x.compact) {  // a column of M (gap: all ones, derivative 0)
+    const int S = a.n_states;
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) {
+      const int j = g * CPG + jj;
+      if (j >= nvalid) continue;
+      const int y = a.tip_states[(size_t)x.b * a.state_stride + c0 + j];
+      if (y < S) {
+        u[jj] = M[(size_t)s * SP + y];
+        if (WITH_D) w[jj] = dM[(size_t)s * SP + y];
+      } else {
+        u[jj] = s < S ? T(1) : T(0);
+      }
+    }
+    return;
+  }
+  T* sM = smat;
+  T* sD = smat + (size_t)SP * KP;
+  for (int t0 = 0; t0 < SP; t0 += KC) {
+    __syncthreads();  // the previous chunk has been read
+    for (int i = threadIdx.x; i < SP * (KC / VN); i += kBigThreads) {
+      const int row = i / (KC / VN), cv = i % (KC / VN);
+      const V m = *reinterpret_cast<const V*>(M + (size_t)row * SP + t0 + cv * VN);
+      *reinterpret_cast<V*>(sM + (size_t)row * KP + cv * VN) = m;
+      if (WITH_D) {
+        const V d = *reinterpret_cast<const V*>(dM + (size_t)row * SP + t0 + cv * VN);
+        *reinterpret_cast<V*>(sD + (size_t)row * KP + cv * VN) = d;
+      }
+    }
+    for (int i = threadIdx.x; i < CT * (KC / VN); i += kBigThreads) {
+      const int j = i / (KC / VN), cv = i % (KC / VN);
+      V v;
+      if (j < nvalid) v = *reinterpret_cast<const V*>(x.src + (size_t)j * x.stride + t0 + cv * VN);
+      else v = V{};
+      *reinterpret_cast<V*>(svec + j * KC + cv * VN) = v;
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int tt = 0; tt < KC; tt += VN) {
+      const V m = *reinterpret_cast<const V*>(sM + (size_t)s * KP + tt);
+      V d{};
+      if (WITH_D) d = *reinterpret_cast<const V*>(sD + (size_t)s * KP + tt);
+#pragma unroll
+      for (int jj = 0; jj < CPG; ++jj) {
+        const V v = *reinterpret_cast<const V*>(svec + (g * CPG + jj) * KC + tt);
+        u[jj] = big_dot(m, v, u[jj]);
+        if (WITH_D) w[jj] = big_dot(d, v, w[jj]);
+      }
+    }
+  }
+}
+
+// q[jj] = (M' a_j)[t] for t = s, a_j = A[j][*] in shared memory.  Every
+// thread of the block calls this (it synchronises).
+template <typename T, int SP>
+__device__ __forceinline__ void big_col_mv(const T* __restrict__ M, const T* A, T* smat, int g, int s,
+                           T (&q)[BigPlan<T, SP>::CPG]) {
+  using PL = BigPlan<T, SP>;
+  constexpr int CPG = PL::CPG, KC = PL::KC;
+  using V = typename BigVec<T, T>::type;
+  constexpr int VN = BigVec<T, T>::n;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) q[jj] = T(0);
+  for (int s0 = 0; s0 < SP; s0 += KC) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < KC * (SP / VN); i += kBigThreads) {
+      const int row = i / (SP / VN), cv = i % (SP / VN);
+      *reinterpret_cast<V*>(smat + (size_t)row * SP + cv * VN) =
+          *reinterpret_cast<const V*>(M + (size_t)(s0 + row) * SP + cv * VN);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ss = 0; ss < KC; ++ss) {
+      const T m = smat[(size_t)ss * SP + s];
+#pragma unroll
+      for (int jj = 0; jj < CPG; ++jj) q[jj] = fma(m, A[(size_t)(g * CPG + jj) * SP + s0 + ss], q[jj]);
+    }
+  }
+}
+
+// x[jj] summed (or maximised) over the S_pad threads of the group, in a
+// fixed order; every thread of the group receives the result.
+template <typename T, int SP, bool MAX>
+__device__ __forceinline__ void big_group_reduce(T (&x)[BigPlan<T, SP>::CPG], T* red, int g, int s) {
+  using PL = BigPlan<T, SP>;
+  constexpr int CPG = PL::CPG, WPG = PL::WPG;
+  const int lane = threadIdx.x & 31, wig = s >> 5;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    T v = x[jj];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T y = __shfl_xor_sync(kFull, v, o);
+      v = MAX ? tmax(v, y) : v + y;
+    }
+    if (lane == 0) red[(g * CPG + jj) * WPG + wig] = v;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    T v = red[(g * CPG + jj) * WPG];
+    for (int i = 1; i < WPG; ++i) {
+      const T y = red[(g * CPG + jj) * WPG + i];
+      v = MAX ? tmax(v, y) : v + y;
+    }
+    x[jj] = v;
+  }
+  __syncthreads();
+}
+
+template <typename T, int SP>
+__global__ void __launch_bounds__(kBigThreads, 1) post_big_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();
+  using PL = BigPlan<T, SP>;
+  constexpr int CT = PL::CT, CPG = PL::CPG;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* smat = reinterpret_cast<T*>(smraw);
+  T* svec = smat + PL::mat;
+  T* red = svec + PL::vec;
+  __shared__ double lred[kBigThreads / SP];
+  const int k = a.level_nodes[blockIdx.y];
+  const int2 ch = a.children[k];
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int c0 = blockIdx.x * CT, nvalid = min(CT, C - c0);
+  const int s = threadIdx.x % SP, g = threadIdx.x / SP;
+  const size_t msz = (size_t)SP * SP;
+  T mx[CPG], lsum[CPG];
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) { mx[jj] = T(0); lsum[jj] = T(0); }
+  const T pis = s < S ? (T)a.root_pi[s] : T(0);
+  for (int r = 0; r < R; ++r) {
+    T ui[CPG], uj[CPG], dummy[CPG];
+    const BigChild<T> xi = big_child(a, ch.x, c0, r, SP), xj = big_child(a, ch.y, c0, r, SP);
+    big_row_mv<T, SP, false>(a, xi, a.P + ((size_t)ch.x * R + r) * msz, nullptr, c0, nvalid,
+                             smat, svec, g, s, ui, dummy);
+    big_row_mv<T, SP, false>(a, xj, a.P + ((size_t)ch.y * R + r) * msz, nullptr, c0, nvalid,
+                             smat, svec, g, s, uj, dummy);
+    const T wr = a.cat_wt[r];
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) {
+      const int j = g * CPG + jj;
+      const T p = ui[jj] * uj[jj];
+      mx[jj] = tmax(mx[jj], fabs(p));
+      if (k == a.root) lsum[jj] = fma(wr * pis, p, lsum[jj]);
+      else if (j < nvalid)
+        a.post[(((size_t)(k - a.n_tips) * C + c0 + j) * R + r) * SP + s] = p;
+    }
+  }
+  big_group_reduce<T, SP, true>(mx, red, g, s);
+  if (k == a.root) big_group_reduce<T, SP, false>(lsum, red, g, s);
+  double lterm = 0.0;
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj, c = c0 + j;
+    if (j >= nvalid) continue;
+    int e = 0;
+    if (!(mx[jj] > T(0)) || !isfinite(mx[jj])) {
+      if (s == 0) atomicOr(a.err, ERR_ZERO_PARTIAL);
+    } else {
+      (void)frexp(mx[jj], &e);
+    }
+    const T f = ldexp(T(1), -e);
+    int ec = e;
+    if (ch.x >= a.n_tips) ec += a.escale[(size_t)(ch.x - a.n_tips) * a.escale_stride + c];
+    if (ch.y >= a.n_tips) ec += a.escale[(size_t)(ch.y - a.n_tips) * a.escale_stride + c];
+    if (k != a.root) {
+      T* out = a.post + (((size_t)(k - a.n_tips) * C + c) * R) * SP + s;
+      for (int r = 0; r < R; ++r) out[(size_t)r * SP] *= f;
+      if (s == 0) a.escale[(size_t)(k - a.n_tips) * a.escale_stride + c] = ec;
+    } else if (s == 0) {
+      // Eq. 3: L_c = sum_r w_r pi' p_root,r (scaled by f), exponents restored
+      const double L = (double)(lsum[jj] * f);
+      if (!(L > 0.0) || !isfinite(L)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      lterm += a.pattern_w[c] * (log(L) + (double)ec * 0.69314718055994530942);
+    }
+  }
+  if (k == a.root) {
+    if (s == 0) lred[g] = lterm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double l = 0.0;
+      for (int i = 0; i < PL::G; ++i) l += lred[i];
+      a.lpart[blockIdx.x] = l;
+    }
+  }
+}
+
+template <typename T, int SP>
+__global__ void __launch_bounds__(kBigThreads, 1) pre_big_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();
+  using PL = BigPlan<T, SP>;
+  constexpr int CT = PL::CT, CPG = PL::CPG;
+  using A = Acc<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* smat = reinterpret_cast<T*>(smraw);
+  T* svec = smat + PL::mat;
+  T* U = svec + PL::vec;            // [CT][SP]: u_i, then a_i
+  T* W = U + (size_t)CT * SP;       // [CT][SP]: w_i, then a_j
+  T* red = W + (size_t)CT * SP;
+  __shared__ typename A::type gred[kBigThreads / SP][2];
+  const int k = a.level_nodes[blockIdx.y];
+  const int2 ch = a.children[k];
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int c0 = blockIdx.x * CT, nvalid = min(CT, C - c0);
+  const int s = threadIdx.x % SP, g = threadIdx.x / SP;
+  const size_t msz = (size_t)SP * SP;
+  const bool int_i = ch.x >= a.n_tips, int_j = ch.y >= a.n_tips;
+  T ni[CPG], nj[CPG], dd[CPG], mi[CPG], mj[CPG];
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) { ni[jj] = nj[jj] = dd[jj] = mi[jj] = mj[jj] = T(0); }
+  for (int r = 0; r < R; ++r) {
+    const size_t mi_off = ((size_t)ch.x * R + r) * msz, mj_off = ((size_t)ch.y * R + r) * msz;
+    T u[CPG], w[CPG];
+    const BigChild<T> xi = big_child(a, ch.x, c0, r, SP), xj = big_child(a, ch.y, c0, r, SP);
+    big_row_mv<T, SP, true>(a, xi, a.P + mi_off, a.dP + mi_off, c0, nvalid, smat, svec, g, s, u, w);
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) {
+      U[(size_t)(g * CPG + jj) * SP + s] = u[jj];
+      W[(size_t)(g * CPG + jj) * SP + s] = w[jj];
+    }
+    big_row_mv<T, SP, true>(a, xj, a.P + mj_off, a.dP + mj_off, c0, nvalid, smat, svec, g, s, u, w);
+    const T wr = a.cat_wt[r];
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) {
+      const int j = g * CPG + jj;
+      T q = T(0);
+      if (k == a.root) q = s < S ? (T)a.root_pi[s] : T(0);
+      else if (j < nvalid) q = a.pre[(((size_t)(k - a.n_tips) * C + c0 + j) * R + r) * SP + s];
+      const size_t o = (size_t)j * SP + s;
+      const T ui = U[o], wi = W[o];
+      const T ai = q * u[jj], aj = q * ui;  // a_i = q o P_j p_j, a_j = q o P_i p_i
+      ni[jj] = fma(wr, ai * wi, ni[jj]);
+      nj[jj] = fma(wr, aj * w[jj], nj[jj]);
+      dd[jj] = fma(wr, ai * ui, dd[jj]);
+      U[o] = ai;
+      W[o] = aj;
+    }
+    // Eq. 4 for internal children: q_x = P_x' a_x (unscaled for now)
+    for (int x = 0; x < 2; ++x) {
+      if (!(x == 0 ? int_i : int_j)) continue;
+      T q[CPG];
+      big_col_mv<T, SP>(a.P + (x == 0 ? mi_off : mj_off), x == 0 ? U : W, smat, g, s, q);
+      const int b = x == 0 ? ch.x : ch.y;
+#pragma unroll
+      for (int jj = 0; jj < CPG; ++jj) {
+        const int j = g * CPG + jj;
+        if (x == 0) mi[jj] = tmax(mi[jj], fabs(q[jj]));
+        else mj[jj] = tmax(mj[jj], fabs(q[jj]));
+        if (j < nvalid) a.pre[(((size_t)(b - a.n_tips) * C + c0 + j) * R + r) * SP + s] = q[jj];
+      }
+    }
+    __syncthreads();  // U and W are rewritten by the next category
+  }
+  big_group_reduce<T, SP, false>(ni, red, g, s);
+  big_group_reduce<T, SP, false>(nj, red, g, s);
+  big_group_reduce<T, SP, false>(dd, red, g, s);
+  if (int_i) big_group_reduce<T, SP, true>(mi, red, g, s);
+  if (int_j) big_group_reduce<T, SP, true>(mj, red, g, s);
+  typename A::type gi = A::zero(), gj = A::zero();
+#pragma unroll
+  for (int jj = 0; jj < CPG; ++jj) {
+    const int j = g * CPG + jj, c = c0 + j;
+    if (j >= nvalid) continue;
+    if (s == 0) {
+      if (!(dd[jj] > T(0)) || !isfinite(dd[jj])) {
+        atomicOr(a.err, ERR_BAD_RATIO);
+      } else {
+        gi = A::add(gi, A::prod(a.pattern_wt[c], ni[jj] / dd[jj]));
+        gj = A::add(gj, A::prod(a.pattern_wt[c], nj[jj] / dd[jj]));
+      }
+    }
+    for (int x = 0; x < 2; ++x) {
+      if (!(x == 0 ? int_i : int_j)) continue;
+      const T m = x == 0 ? mi[jj] : mj[jj];
+      int e = 0;
+      if (!(m > T(0)) || !isfinite(m)) {
+        if (s == 0) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      } else {
+        (void)frexp(m, &e);
+      }
+      const T f = ldexp(T(1), -e);
+      const int b = x == 0 ? ch.x : ch.y;
+      T* out = a.pre + (((size_t)(b - a.n_tips) * C + c) * R) * SP + s;
+      for (int r = 0; r < R; ++r) out[(size_t)r * SP] *= f;
+    }
+  }
+  if (s == 0) { gred[g][0] = gi; gred[g][1] = gj; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gi = gred[0][0];
+    gj = gred[0][1];
+    for (int i = 1; i < PL::G; ++i) {
+      gi = A::add(gi, gred[i][0]);
+      gj = A::add(gj, gred[i][1]);
+    }
+    a.gpart[(size_t)ch.x * a.n_tiles + blockIdx.x] = A::to_double(gi);
+    a.gpart[(size_t)ch.y * a.n_tiles + blockIdx.x] = A::to_double(gj);
+  }
+}
+
+template <typename T, int SP>
+cudaError_t launch_big(const LevelArgs<T>& a, bool post, cudaStream_t st) {
+  dim3 grid(a.n_tiles, a.n_level);
+  using PL = BigPlan<T, SP>;
+  if (post) return launch_pdl(post_big_kernel<T, SP>, grid, kBigThreads, PL::bytes(false), st, a);
+  return launch_pdl(pre_big_kernel<T, SP>, grid, kBigThreads, PL::bytes(true), st, a);
+}
+
+template <typename T, int SP>
+cudaError_t prepare_big() {
+  using PL = BigPlan<T, SP>;
+  cudaError_t e = cudaFuncSetAttribute(post_big_kernel<T, SP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)PL::bytes(false));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(pre_big_kernel<T, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)PL::bytes(true));
+}
+
+}  // namespace phylo

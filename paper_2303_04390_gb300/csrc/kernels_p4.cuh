@@ -223,10 +223,10 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
   // child x's P', dP' and P of category r
   const float4* PTi = sm.m[0];
   const float4* PTj = sm.m[1];
-  const float4* DTi = sm.m[0] + 4 * R;
-  const float4* DTj = sm.m[1] + 4 * R;
-  const float4* Pi = sm.m[0] + 8 * R;
-  const float4* Pj = sm.m[1] + 8 * R;
+  const float4* DTi = sm.m[0] + (PRE ? 4 * R : 0);  // (post-order: unused)
+  const float4* DTj = sm.m[1] + (PRE ? 4 * R : 0);
+  const float4* Pi = sm.m[0] + (PRE ? 8 * R : 0);
+  const float4* Pj = sm.m[1] + (PRE ? 8 * R : 0);
   if constexpr (CH) {
     // a cherry child's partials from its two tip states
 #pragma unroll

@@ -64,7 +64,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
                            Layout* Lp) {
   if (N < 2 || N > 65536) return "n_tips must be in [2, 65536]";
   if (C < 0) return "n_patterns must be >= 0";
-  if (S < 2 || S > 64) return "n_states must be in [2, 64]";
+  if (S < 2 || S > kMaxStates) return "n_states must be in [2, 256]";
   if (R < 1 || R > 8) return "n_categories must be in [1, 8]";
   if (prec != PHYLO_FP64 && prec != PHYLO_FP32) return "unknown precision";
   if (flags & ~(PHYLO_FLAG_TIP_PARTIALS | PHYLO_FLAG_NO_GRAPH)) return "unknown flags";
@@ -872,7 +872,7 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
 
 int phylo_eigen_reversible(int S, const double* Q, const double* pi, double* V,
                            double* Vinv, double* lambda) {
-  if (S < 2 || S > 64) return fail(nullptr, PHYLO_EINVAL, "n_states must be in [2, 64]");
+  if (S < 2 || S > kMaxStates) return fail(nullptr, PHYLO_EINVAL, "n_states must be in [2, 256]");
   if (!Q || !pi || !V || !Vinv || !lambda) return fail(nullptr, PHYLO_EINVAL, "NULL argument");
   double qmax = 0.0, psum = 0.0;
   for (int i = 0; i < S; ++i) {

@@ -29,7 +29,9 @@ __host__ __device__ inline int round_up(int x, int m) { return (x + m - 1) / m *
 inline int padded_states(int S) {
   if (S <= 4) return 4;
   if (S <= 20) return 20;
-  return 64;
+  if (S <= 64) return 64;
+  if (S <= 128) return 128;
+  return 256;
 }
 
 // Lanes per pattern in the register kernels (next power of two >= R).
@@ -45,6 +47,10 @@ constexpr int kSmallThreads = 128;
 constexpr int kWideThreads = 256;
 constexpr int kWidePatternsF32 = 16;
 constexpr int kWidePatternsF64 = 8;
+// Patterns per block of the kernels for S_pad = 128 and 256 (kernels_big.cuh).
+constexpr int kBigPatternsF32 = 16;
+constexpr int kBigPatternsF64 = 8;
+constexpr int kMaxStates = 256;
 
 // Patterns per block of the FP32 4-state kernels (kernels_p4.cuh), one
 // thread per pattern.
@@ -110,6 +116,7 @@ inline int patterns_per_tile(int SP, int R, bool fp64) {
   if (SP == 4 && !fp64) return kP4TilePatterns;
   if (uses_tensor_cores(SP, fp64)) return kTcTilePatterns;
   if (SP <= 20) return kSmallThreads / lanes_per_pattern(R);
+  if (SP >= 128) return fp64 ? kBigPatternsF64 : kBigPatternsF32;
   return fp64 ? kWidePatternsF64 : kWidePatternsF32;
 }
 

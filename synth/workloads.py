@@ -231,6 +231,42 @@ def codon_gy94(kappa: float, omega: float, pi: np.ndarray):
     return _reversible_q(ex, pi), pi
 
 
+def markov_modulated(components, pis_class, switch_rate: float):
+    """Markov-modulated model (the paper's 122-state MMM of two codon
+    models, Results): K reversible component generators on the same S
+    states and frequencies pi, combined on the K*S states (k, i).  Within
+    class k substitutions follow Q_k; the class switches (k, i) -> (l, i)
+    at rate switch_rate * rho_l.  The stationary distribution is
+    rho_k pi_i and the combined generator is reversible; it is rescaled to
+    mean rate 1 like every model here."""
+    K = len(components)
+    S = components[0][0].shape[0]
+    pi = np.asarray(components[0][1], dtype=np.float64)
+    rho = np.asarray(pis_class, dtype=np.float64)
+    assert rho.shape == (K,) and abs(rho.sum() - 1.0) < 1e-12
+    ex = np.zeros((K * S, K * S))
+    for k, (Qk, pik) in enumerate(components):
+        assert np.allclose(pik, pi)
+        exk = Qk / pi[None, :]  # Q_k[i][j] = ex_k[i][j] pi_j off the diagonal
+        np.fill_diagonal(exk, 0.0)
+        ex[k * S:(k + 1) * S, k * S:(k + 1) * S] = exk / rho[k]
+    for k in range(K):
+        for l in range(K):
+            if k != l:
+                idx = np.arange(S)
+                ex[k * S + idx, l * S + idx] = switch_rate / pi
+    pi_full = (rho[:, None] * pi[None, :]).reshape(-1)
+    return _reversible_q(ex, pi_full), pi_full
+
+
+def codon_mmm(kappa: float, omegas, pi: np.ndarray, switch_rate: float = 0.5):
+    """Two (or more) GY94-style codon models differing in omega, modulated
+    with equal class weights: 61 * len(omegas) states."""
+    comps = [codon_gy94(kappa, om, pi) for om in omegas]
+    return markov_modulated(comps, np.full(len(omegas), 1.0 / len(omegas)),
+                            switch_rate)
+
+
 def discrete_gamma(alpha: float, n_cat: int):
     """Yang (1994) discrete Gamma: equal-probability bins of Gamma(alpha,
     rate alpha), each category rate the mean of its bin (mean rate 1).
@@ -442,6 +478,27 @@ def workload_aa_256(seed: int = 0, n_tips: int = 256,
                     Q, pi, rates, w, pats, pw, "fp32")
 
 
+def workload_mmm_122(seed: int = 0, n_tips: int = 128,
+                     n_patterns: int = 2000) -> Workload:
+    """The codon workload's shape with the paper's Markov-modulated model:
+    two GY94-style codon models (kappa 2, omega 0.1 and 1.0, codon
+    frequencies ~ Dirichlet(61 x 1)) switching at rate 0.5, 122 states;
+    128-taxon Yule tree, Exp(mean 0.05) branches, Gamma 4 categories
+    (alpha 0.5), 2,000 unique patterns, weights 1..5."""
+    rng = np.random.default_rng([seed, 6])
+    parent = yule_tree(n_tips, rng)
+    t = exponential_branch_lengths(n_tips, 0.05, rng)
+    pi = rng.dirichlet(np.ones(61))
+    pi = np.maximum(pi, 1e-4)
+    pi /= pi.sum()
+    Q, pi = codon_mmm(2.0, (0.1, 1.0), pi)
+    rates, w = discrete_gamma(0.5, 4)
+    pats = unique_patterns(parent, t, Q, pi, rates, w, n_patterns, rng)
+    pw = rng.integers(1, 6, size=n_patterns).astype(np.float64)
+    return Workload(f"mmm-codon122-g4-{n_tips}taxa-{n_patterns}patterns",
+                    parent, t, Q, pi, rates, w, pats, pw, "fp32")
+
+
 def small_workload(n_tips: int, n_states: int, n_cat: int, n_patterns: int,
                    seed: int, mean_t: float = 0.1,
                    tree: str = "yule", unique: bool = False) -> Workload:
@@ -456,11 +513,14 @@ def small_workload(n_tips: int, n_states: int, n_cat: int, n_patterns: int,
     t = exponential_branch_lengths(n_tips, mean_t, rng)
     if n_states == 4:
         Q, pi = hky85(4.0, rng.dirichlet([10.0] * 4))
-    elif n_states == 61:
+    elif n_states in (61, 122):
         pi = rng.dirichlet(np.ones(61))
         pi = np.maximum(pi, 1e-4)
         pi /= pi.sum()
-        Q, pi = codon_gy94(2.0, 0.3, pi)
+        if n_states == 61:
+            Q, pi = codon_gy94(2.0, 0.3, pi)
+        else:
+            Q, pi = codon_mmm(2.0, (0.1, 1.0), pi)
     else:
         Q, pi = random_reversible(n_states, rng)
     rates, w = discrete_gamma(0.5, n_cat)
@@ -478,6 +538,7 @@ CONFIGS = {
     "hky-1024": workload_hky_1024,
     "codon-128": workload_codon_128,
     "aa-256": workload_aa_256,
+    "mmm-122": workload_mmm_122,
 }
 
 

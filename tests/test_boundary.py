@@ -60,7 +60,7 @@ def test_workspace_bytes(lib):
 
 
 @pytest.mark.parametrize("args", [(1, 10, 4, 1), (8, -1, 4, 1), (8, 10, 1, 1),
-                                  (8, 10, 65, 1), (8, 10, 4, 0), (8, 10, 4, 9),
+                                  (8, 10, 257, 1), (8, 10, 4, 0), (8, 10, 4, 9),
                                   (70000, 10, 4, 1)])
 def test_workspace_bytes_rejects_bad_sizes(lib, args):
     out = ctypes.c_size_t(0)
@@ -185,7 +185,7 @@ def test_eigen_validation(lib):
     lib.phylo_destroy(ctx)
 
 
-@pytest.mark.parametrize("S", [2, 4, 7, 20, 33, 61, 64])
+@pytest.mark.parametrize("S", [2, 4, 7, 20, 33, 61, 64, 122, 256])
 def test_host_eigendecomposition(lib, S):
     """V diag(lambda) Vinv reproduces Q; exp via the eigenvalues matches the
     library matrix exponential; one eigenvalue is exactly 0."""

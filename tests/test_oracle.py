@@ -60,6 +60,28 @@ def test_transition_matrix_properties():
             assert Pt.min() > -1e-15
 
 
+def test_large_state_spaces():
+    """The 122-state Markov-modulated codon model and a 256-state model:
+    P from the oracle against the library matrix exponential, P(0) = I,
+    rows summing to 1, stationarity and detailed balance."""
+    rng = np.random.default_rng(9)
+    pi = rng.dirichlet(np.ones(61))
+    pi = np.maximum(pi, 1e-4)
+    for Q, pi_ in [synth.codon_mmm(2.0, (0.1, 1.0), pi / pi.sum()),
+                   synth.random_reversible(256, rng)]:
+        S = Q.shape[0]
+        assert np.allclose(Q.sum(axis=1), 0.0, atol=1e-13)
+        assert abs(-np.dot(pi_, np.diag(Q)) - 1.0) < 1e-12
+        np.testing.assert_array_equal(O.expm_taylor(0.0 * Q), np.eye(S))
+        for t in [1e-3, 0.05, 0.7]:
+            P = O.expm_taylor(t * Q)
+            np.testing.assert_allclose(P, scipy.linalg.expm(t * Q), atol=1e-13)
+            np.testing.assert_allclose(P.sum(axis=1), 1.0, atol=1e-13)
+            np.testing.assert_allclose(pi_ @ P, pi_, atol=1e-13)
+            D = pi_[:, None] * P
+            np.testing.assert_allclose(D, D.T, atol=1e-14)
+
+
 def test_transition_derivative_by_finite_difference():
     rng = np.random.default_rng(3)
     rates = np.array([0.3, 1.7])
@@ -175,7 +197,7 @@ def _fd_gradient(w, h_rel=1e-4):
 
 
 @pytest.mark.parametrize("n_tips,n_states,ncat", [(8, 4, 4), (5, 20, 2),
-                                                   (4, 61, 2)])
+                                                   (4, 61, 2), (4, 122, 2)])
 def test_gradient_matches_finite_differences(n_tips, n_states, ncat):
     w = synth.small_workload(n_tips, n_states, ncat, 25, seed=4, mean_t=0.15)
     _, grad, abs_sum = O.evaluate(w.parent, w.t, w.Q, w.pi, w.rates,

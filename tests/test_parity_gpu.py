@@ -62,6 +62,13 @@ SMALL = [
     (6, 45, 3, 129, "caterpillar"),    # a tail of one pattern
     (40, 61, 4, 1, "yule"),
     (120, 61, 4, 130, "caterpillar"),  # deep chain: rescaling at every node
+    # 65..256 states (S_pad 128, 256): matrices streamed through shared memory
+    (6, 122, 4, 40, "yule"),
+    (9, 122, 2, 33, "caterpillar"),
+    (20, 122, 4, 50, "yule"),
+    (7, 90, 3, 17, "balanced"),
+    (5, 256, 2, 19, "yule"),
+    (8, 200, 1, 9, "caterpillar"),
 ]
 
 
@@ -72,14 +79,15 @@ def test_small_parity(shape, precision):
     w = synth.small_workload(n, S, R, C, seed=21, mean_t=0.15, tree=tree)
     rng = np.random.default_rng(5)
     gaps = rng.random(w.tip_states.shape) < 0.05
-    w.tip_states[gaps] = S
+    if S < 256:  # 256 states use every byte value: no gap code
+        w.tip_states[gaps] = S
     ref = oracle_eval(w)
     _, logL, grad = _gpu(w, precision)
     compare(logL, grad, ref, precision, w.name)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("S", [4, 20, 61])
+@pytest.mark.parametrize("S", [4, 20, 61, 122])
 def test_tip_partials(S, precision):
     w = synth.small_workload(11, S, 4, 45, seed=22)
     from oracle import phylo_oracle as O
@@ -93,7 +101,7 @@ def test_tip_partials(S, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("S", [4, 61])
+@pytest.mark.parametrize("S", [4, 61, 122])
 def test_zero_length_branches(S, precision):
     w = synth.small_workload(15, S, 4, 80, seed=23)
     t = w.t.copy()
@@ -107,7 +115,7 @@ def test_zero_length_branches(S, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("S", [4, 20, 61])
+@pytest.mark.parametrize("S", [4, 20, 61, 256])
 def test_empty_alignment(S, precision):
     w = synth.small_workload(6, S, 2, 10, seed=24)
     w = w.with_patterns(0, 0)
@@ -227,6 +235,7 @@ FULL = {
     "hky-1024": ("fp32", 8),
     "codon-128": ("fp32", 8),
     "aa-256": ("fp32", 8),
+    "mmm-122": ("fp32", 8),  # the 122-state Markov-modulated model, codon shape
 }
 
 
