@@ -501,6 +501,31 @@ def run_ours(args):
         "launches_per_evaluation": n_launch_dom,
         "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
     }
+    if w.n_states > 64:
+        # 65..256 states: the level kernels are CUDA-core contractions
+        # (about 2 S flop per byte moved), so the bound is the FP32 (FP64)
+        # arithmetic rate: SMs x 128 FP32 lanes x 2 flop x the maximum SM
+        # clock; FP64 takes the GB300's nominal 1.25 TFLOP/s
+        fl = algorithmic_flops(w)
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = peaks.get("sm_max_mhz") or 2070.0
+        if precision == "fp32":
+            apeak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+            akind = f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
+        else:
+            apeak, akind = 1.25, "nominal FP64 rate"
+        aach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
+        roofline = {
+            "bound": "alu", "kernel": kernels[dom], "achieved": aach, "peak": apeak,
+            "unit": "TFLOP/s", "frac": aach / apeak, "peak_kind": akind,
+            "traffic": traffic,
+            "algorithmic_flops_per_launch": fl[dom] / n_launch_dom,
+            "launches_per_evaluation": n_launch_dom,
+            "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
+            "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak,
+                    "algorithmic_bytes_per_launch": by[dom] / n_launch_dom},
+        }
     tensor = None
     if precision == "fp32" and 20 < w.n_states <= 64:
         # the tensor-core path: algorithmic FLOP rate of its dominant phase

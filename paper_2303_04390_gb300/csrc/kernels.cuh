@@ -962,9 +962,9 @@ inline size_t wide_pre_smem(int R) {
 
 }  // namespace phylo
 
-#include "kernels_big.cuh"
 #include "kernels_p4.cuh"
 #include "kernels_tc64.cuh"
+#include "kernels_big.cuh"
 
 namespace phylo {
 
@@ -1094,8 +1094,14 @@ cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
       if constexpr (std::is_same<T, float>::value) return launch_pmat_tc64(a, st);
       else pmat_kernel<T, 64><<<units, 256, 0, st>>>(a);
       break;
-    case 128: pmat_kernel<T, 128><<<units, 256, 0, st>>>(a); break;
-    case 256: pmat_kernel<T, 256><<<units, 256, 0, st>>>(a); break;
+    case 128:
+      if constexpr (std::is_same<T, float>::value) return launch_pmat_big<128>(a, st);
+      else pmat_kernel<T, 128><<<units, 256, 0, st>>>(a);
+      break;
+    case 256:
+      if constexpr (std::is_same<T, float>::value) return launch_pmat_big<256>(a, st);
+      else pmat_kernel<T, 256><<<units, 256, 0, st>>>(a);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -22,9 +22,15 @@
 namespace phylo {
 
 constexpr int kBigThreads = 256;
+// Two resident blocks for S_pad = 128 (registers capped at 128, no spills),
+// one for 256.  Measured on the 122-state workload (FP32): 8-pattern tiles
+// with 64-column chunks and two blocks per SM ran the level kernels at
+// 3.4 + 7.9 ms per evaluation, against 5.8 + 11.8 ms for 16-pattern tiles,
+// 32-column chunks and one block.
+template <int SP> constexpr int kBigMinBlocks = SP == 128 ? 2 : 1;
 template <typename T> struct BigCfg;
 template <> struct BigCfg<float> {
-  static constexpr int CT = kBigPatternsF32, KC = 32;
+  static constexpr int CT = kBigPatternsF32, KC = 64;
 };
 template <> struct BigCfg<double> {
   static constexpr int CT = kBigPatternsF64, KC = 16;
@@ -211,7 +217,7 @@ __device__ __forceinline__ void big_group_reduce(T (&x)[BigPlan<T, SP>::CPG], T*
 }
 
 template <typename T, int SP>
-__global__ void __launch_bounds__(kBigThreads, 1) post_big_kernel(LevelArgs<T> a) {
+__global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) post_big_kernel(LevelArgs<T> a) {
   pdl_wait_and_release();
   using PL = BigPlan<T, SP>;
   constexpr int CT = PL::CT, CPG = PL::CPG;
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(kBigThreads, 1) post_big_kernel(LevelArgs<T> a
 }
 
 template <typename T, int SP>
-__global__ void __launch_bounds__(kBigThreads, 1) pre_big_kernel(LevelArgs<T> a) {
+__global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) pre_big_kernel(LevelArgs<T> a) {
   pdl_wait_and_release();
   using PL = BigPlan<T, SP>;
   constexpr int CT = PL::CT, CPG = PL::CPG;
@@ -417,6 +423,161 @@ cudaError_t prepare_big() {
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(pre_big_kernel<T, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)PL::bytes(true));
+}
+
+}  // namespace phylo
+
+namespace phylo {
+
+// ---------------------------------------------------------------------------
+// Transition matrices for S_pad 128 and 256 on the FP32 path (Eq. 1):
+// P - I = V diag(e^{lambda gamma t} - 1) Vinv and dP = V diag(gamma lambda
+// e^{lambda gamma t}) Vinv in the double-float arithmetic of the 64-state
+// build (kernels_tc64.cuh: Dekker products, Knuth sums, ~48 bits), so that
+// the small entries of short branches keep FP32 accuracy through the
+// cancellation in the sum over eigenvalues.  A CTA computes one 64 x 64
+// tile of P and dP of one (branch, category), streaming the double-float
+// eigenvector tables through shared memory kPmatBigChunk eigenvalues at a
+// time; each thread owns a 4 x 4 block.  For the symmetric decomposition
+// of a reversible model (Vinv[m][t] = pi_t V[t][m]) P - I = K diag(pi) with
+// K = V diag(e) V' symmetric: only the tiles on and above the diagonal are
+// contracted, and an off-diagonal tile also writes its mirror.
+// ---------------------------------------------------------------------------
+constexpr int kPmatBigChunk = 32;
+
+template <int SP>
+__global__ void __launch_bounds__(256) pmat_big_df_kernel(PmatArgs a) {
+  constexpr int T = SP / 64;
+  __shared__ __align__(16) float sv_h[kPmatBigChunk][64], sv_l[kPmatBigChunk][64];
+  __shared__ __align__(16) float sw_h[kPmatBigChunk][64], sw_l[kPmatBigChunk][64];
+  __shared__ DF se[SP], sd[SP];
+  const int S = a.n_states, R = a.n_cat, tid = threadIdx.x;
+  const bool rev = a.reversible != 0;
+  const int nt = rev ? T * (T + 1) / 2 : T * T;
+  const int unit = blockIdx.x / nt, tile = blockIdx.x % nt;
+  int sb, tb;
+  if (rev) {  // tile -> (sb, tb), sb <= tb, row by row
+    sb = 0;
+    int rem = tile;
+    while (rem >= T - sb) {
+      rem -= T - sb;
+      ++sb;
+    }
+    tb = sb + rem;
+  } else {
+    sb = tile / T;
+    tb = tile % T;
+  }
+  const int b = unit / R, r = unit % R;
+  for (int i = tid; i < SP; i += 256) {
+    double e = 0.0, de = 0.0;
+    if (i < S) {
+      double t = a.t[b];
+      if (!(t >= 0.0) || !isfinite(t)) {
+        if (i == 0 && r == 0 && tile == 0) atomicOr(a.err, ERR_BAD_LENGTH);
+        t = 0.0;
+      }
+      const double g = a.rates[r];
+      const double x = a.lambda[i] * g * t;
+      e = expm1(x);
+      de = g * a.lambda[i] * exp(x);
+    }
+    se[i] = df_from(e);
+    sd[i] = df_from(de);
+  }
+  const size_t sq = (size_t)SP * SP;
+  const float* vt_h = a.vsplit;           // V' : [m][s]
+  const float* vt_l = a.vsplit + sq;
+  const float* w_h = rev ? vt_h : a.vsplit + 2 * sq;  // Vinv [m][t], or V' again
+  const float* w_l = rev ? vt_l : a.vsplit + 3 * sq;
+  const int ls = 4 * (tid / 16), lt = 4 * (tid % 16);  // the thread's block in the tile
+  DF accP[4][4], accD[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accP[i][j] = accD[i][j] = DF{0.f, 0.f};
+  for (int m0 = 0; m0 < S; m0 += kPmatBigChunk) {
+    __syncthreads();  // exponentials staged / previous chunk read
+    for (int i = tid; i < kPmatBigChunk * 16; i += 256) {
+      const int row = i / 16, c4 = 4 * (i % 16);
+      const size_t gs = (size_t)(m0 + row) * SP + 64 * sb + c4;
+      const size_t gt = (size_t)(m0 + row) * SP + 64 * tb + c4;
+      *reinterpret_cast<float4*>(&sv_h[row][c4]) = *reinterpret_cast<const float4*>(vt_h + gs);
+      *reinterpret_cast<float4*>(&sv_l[row][c4]) = *reinterpret_cast<const float4*>(vt_l + gs);
+      *reinterpret_cast<float4*>(&sw_h[row][c4]) = *reinterpret_cast<const float4*>(w_h + gt);
+      *reinterpret_cast<float4*>(&sw_l[row][c4]) = *reinterpret_cast<const float4*>(w_l + gt);
+    }
+    __syncthreads();
+    const int mend = min(kPmatBigChunk, S - m0);
+    for (int mm = 0; mm < mend; ++mm) {
+      const float4 vh = *reinterpret_cast<const float4*>(&sv_h[mm][ls]);
+      const float4 vl = *reinterpret_cast<const float4*>(&sv_l[mm][ls]);
+      const float4 wh = *reinterpret_cast<const float4*>(&sw_h[mm][lt]);
+      const float4 wl = *reinterpret_cast<const float4*>(&sw_l[mm][lt]);
+      const DF em = se[m0 + mm], dm = sd[m0 + mm];
+      const DF v[4] = {{vh.x, vl.x}, {vh.y, vl.y}, {vh.z, vl.z}, {vh.w, vl.w}};
+      const DF w[4] = {{wh.x, wl.x}, {wh.y, wl.y}, {wh.z, wl.z}, {wh.w, wl.w}};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const DF ve = df_mul(v[i], em), vd = df_mul(v[i], dm);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          df_fma(accP[i][j], ve, w[j]);
+          df_fma(accD[i][j], vd, w[j]);
+        }
+      }
+    }
+  }
+  float* P = static_cast<float*>(a.P) + (size_t)unit * sq;
+  float* D = static_cast<float*>(a.dP) + (size_t)unit * sq;
+  const int s0 = 64 * sb + ls, t0 = 64 * tb + lt;
+  const float* pi_h = a.vsplit + 4 * sq;
+  const float* pi_l = pi_h + SP;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int s = s0 + i;
+    float p[4], d[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + j;
+      DF kp = accP[i][j], kd = accD[i][j];
+      if (rev) {
+        const DF pt = {pi_h[t], pi_l[t]};
+        kp = df_mul(kp, pt);
+        kd = df_mul(kd, pt);
+      }
+      p[j] = df_round(kp, s == t && s < S);
+      d[j] = df_round(kd, false);
+    }
+    *reinterpret_cast<float4*>(P + (size_t)s * SP + t0) = make_float4(p[0], p[1], p[2], p[3]);
+    *reinterpret_cast<float4*>(D + (size_t)s * SP + t0) = make_float4(d[0], d[1], d[2], d[3]);
+  }
+  if (rev && sb != tb) {  // mirror tile: P[t][s] = delta + K_st pi_s
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = t0 + j;
+      float p[4], d[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int s = s0 + i;
+        const DF ps = {pi_h[s], pi_l[s]};
+        p[i] = df_round(df_mul(accP[i][j], ps), false);
+        d[i] = df_round(df_mul(accD[i][j], ps), false);
+      }
+      *reinterpret_cast<float4*>(P + (size_t)t * SP + s0) = make_float4(p[0], p[1], p[2], p[3]);
+      *reinterpret_cast<float4*>(D + (size_t)t * SP + s0) = make_float4(d[0], d[1], d[2], d[3]);
+    }
+  }
+}
+
+template <int SP>
+cudaError_t launch_pmat_big(const PmatArgs& a, cudaStream_t st) {
+  constexpr int T = SP / 64;
+  const int nt = a.reversible ? T * (T + 1) / 2 : T * T;
+  const long long blocks = (long long)a.n_branches * a.n_cat * nt;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  pmat_big_df_kernel<SP><<<(unsigned)blocks, 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace phylo

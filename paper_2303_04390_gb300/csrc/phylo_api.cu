@@ -115,7 +115,8 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.pattern_w, (size_t)C * 8);
   ok &= add_region(L, L.V, (size_t)S * S * 8);
   ok &= add_region(L, L.Vinv, (size_t)S * S * 8);
-  if (tc) ok &= add_region(L, L.vsplit, kEigenSplitFloats * sizeof(float));
+  if (uses_eigen_split(L.SP, prec == PHYLO_FP64))
+    ok &= add_region(L, L.vsplit, eigen_split_floats(L.SP) * sizeof(float));
   ok &= add_region(L, L.lambda, (size_t)S * 8);
   ok &= add_region(L, L.pi, (size_t)S * 8);
   ok &= add_region(L, L.rates, (size_t)R * 8);
@@ -857,8 +858,8 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
   if ((rc = upload(ctx, ctx->L.V, V, (size_t)S * S, "upload V"))) return rc;
   if ((rc = upload(ctx, ctx->L.Vinv, Vinv, (size_t)S * S, "upload Vinv"))) return rc;
   if (ctx->L.vsplit.bytes) {
-    std::vector<float> split(kEigenSplitFloats);
-    ctx->eig_reversible = build_eigen_split(S, V, Vinv, pi, split.data());
+    std::vector<float> split(eigen_split_floats(ctx->L.SP));
+    ctx->eig_reversible = build_eigen_split(S, ctx->L.SP, V, Vinv, pi, split.data());
     if ((rc = upload(ctx, ctx->L.vsplit, split.data(), split.size(), "upload V split"))) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }

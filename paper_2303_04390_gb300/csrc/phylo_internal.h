@@ -48,7 +48,7 @@ constexpr int kWideThreads = 256;
 constexpr int kWidePatternsF32 = 16;
 constexpr int kWidePatternsF64 = 8;
 // Patterns per block of the kernels for S_pad = 128 and 256 (kernels_big.cuh).
-constexpr int kBigPatternsF32 = 16;
+constexpr int kBigPatternsF32 = 8;
 constexpr int kBigPatternsF64 = 8;
 constexpr int kMaxStates = 256;
 
@@ -79,10 +79,14 @@ constexpr size_t kTcUnitBytes = 73728;
 // Returns whether the decomposition is the symmetric one of a reversible
 // model, Vinv[m][t] = pi_t V[t][m] (then P(t) = I + V diag(e) V' diag(pi)
 // and P_st pi_s = P_ts pi_t, which the kernel exploits).
+// The same tables for S_pad = 128 and 256 (FP32 matrix build of
+// kernels_big.cuh): each SP x SP, then pi, SP each.
+inline size_t eigen_split_floats(int SP) { return 4 * (size_t)SP * SP + 2 * (size_t)SP; }
 constexpr size_t kEigenSplitFloats = 4 * 64 * 64 + 2 * 64;
-inline bool build_eigen_split(int S, const double* V, const double* Vinv, const double* pi,
-                              float* out) {
-  for (int i = 0; i < (int)kEigenSplitFloats; ++i) out[i] = 0.f;
+inline bool build_eigen_split(int S, int SP, const double* V, const double* Vinv,
+                              const double* pi, float* out) {
+  const size_t sq = (size_t)SP * SP;
+  for (size_t i = 0; i < eigen_split_floats(SP); ++i) out[i] = 0.f;
   double vmax = 0.0;
   for (int i = 0; i < S * S; ++i) vmax = Vinv[i] > vmax ? Vinv[i] : (-Vinv[i] > vmax ? -Vinv[i] : vmax);
   bool reversible = true;
@@ -90,20 +94,22 @@ inline bool build_eigen_split(int S, const double* V, const double* Vinv, const 
     for (int s = 0; s < S; ++s) {
       const double v = V[s * S + m], w = Vinv[m * S + s];
       const float vh = (float)v, wh = (float)w;
-      out[0 * 4096 + m * 64 + s] = vh;
-      out[1 * 4096 + m * 64 + s] = (float)(v - (double)vh);
-      out[2 * 4096 + m * 64 + s] = wh;
-      out[3 * 4096 + m * 64 + s] = (float)(w - (double)wh);
+      out[0 * sq + (size_t)m * SP + s] = vh;
+      out[1 * sq + (size_t)m * SP + s] = (float)(v - (double)vh);
+      out[2 * sq + (size_t)m * SP + s] = wh;
+      out[3 * sq + (size_t)m * SP + s] = (float)(w - (double)wh);
       const double dev = w - pi[s] * v;
       if (!(dev <= 1e-10 * vmax && -dev <= 1e-10 * vmax)) reversible = false;
     }
   for (int s = 0; s < S; ++s) {
     const float ph = (float)pi[s];
-    out[4 * 4096 + s] = ph;
-    out[4 * 4096 + 64 + s] = (float)(pi[s] - (double)ph);
+    out[4 * sq + s] = ph;
+    out[4 * sq + SP + s] = (float)(pi[s] - (double)ph);
   }
   return reversible;
 }
+// FP32 paths whose matrix build uses the double-float tables.
+inline bool uses_eigen_split(int SP, bool fp64) { return !fp64 && SP >= 64; }
 
 // Exponent planes per node: R on the tensor-core path, else 1 (one
 // exponent per (node, pattern) shared by all categories).

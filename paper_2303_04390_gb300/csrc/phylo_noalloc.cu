@@ -306,7 +306,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   static thread_local float vsplit[kEigenSplitFloats];
   bool reversible = false;
   if (L.vsplit.bytes) {
-    reversible = build_eigen_split(S, V, Vinv, root_freqs, vsplit);
+    reversible = build_eigen_split(S, 64, V, Vinv, root_freqs, vsplit);
     NA_TRY(up(L.vsplit, vsplit, sizeof(vsplit)), "upload V split");
   }
   NA_TRY(up(L.lambda, lambda, (size_t)S * 8), "upload lambda");

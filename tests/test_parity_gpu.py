@@ -262,14 +262,15 @@ def test_full_size_workloads(name):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_general_eigen_form(precision):
+@pytest.mark.parametrize("S", [61, 122, 256])
+def test_general_eigen_form(precision, S):
     """Eigenvector columns rescaled: the same P(t), but not the symmetric
     decomposition of a reversible model, so the matrix build takes its
     general form (the symmetric one is what set_rate_matrix produces)."""
     import paper_2303_04390_gb300 as pg
-    w = synth.small_workload(14, 61, 4, 150, seed=77)
+    w = synth.small_workload(14 if S < 256 else 6, S, 4, 150 if S < 256 else 30, seed=77)
     V, Vi, lam = pg.eigen_reversible(w.Q, w.pi)
-    c = np.random.default_rng(7).uniform(0.5, 2.0, 61)
+    c = np.random.default_rng(7).uniform(0.5, 2.0, S)
     ref = oracle_eval(w)
     ctx = pg.from_workload(w, precision)
     ctx.set_eigen(V * c, Vi / c[:, None], lam, w.pi)
