@@ -23,32 +23,37 @@ namespace phylo {
 
 constexpr int kBigThreads = 256;
 // Two resident blocks for S_pad = 128 (registers capped at 128, no spills),
-// one for 256.  Measured on the 122-state workload (FP32): 8-pattern tiles
-// with 64-column chunks and two blocks per SM ran the level kernels at
-// 3.4 + 7.9 ms per evaluation, against 5.8 + 11.8 ms for 16-pattern tiles,
-// 32-column chunks and one block.
+// one for 256.  Measured on the 122-state workload (FP32), post- + pre-order
+// ms per evaluation: 16-pattern tiles, 32-column chunks staged through
+// registers, one block per SM: 5.8 + 11.8; 8-pattern tiles, 64-column
+// chunks, two blocks: 3.4 + 7.9; the same with asynchronous copies into two
+// 32-column buffers: 2.8 + 6.9.
 template <int SP> constexpr int kBigMinBlocks = SP == 128 ? 2 : 1;
 template <typename T> struct BigCfg;
+// KC: matrix columns (rows) per chunk; ST: chunk buffers (2: the next
+// chunk's copies fly while the current one is used).
 template <> struct BigCfg<float> {
-  static constexpr int CT = kBigPatternsF32, KC = 64;
+  static constexpr int CT = kBigPatternsF32, KC = 32, ST = 2;
 };
 template <> struct BigCfg<double> {
-  static constexpr int CT = kBigPatternsF64, KC = 16;
+  static constexpr int CT = kBigPatternsF64, KC = 16, ST = 2;
 };
 
 // Shared-memory plan of one block (element counts of T).
 template <typename T, int SP>
 struct BigPlan {
-  static constexpr int CT = BigCfg<T>::CT, KC = BigCfg<T>::KC;
+  static constexpr int CT = BigCfg<T>::CT, KC = BigCfg<T>::KC, ST = BigCfg<T>::ST;
   static constexpr int G = kBigThreads / SP, CPG = CT / G;
   static constexpr int KP = KC + 16 / (int)sizeof(T);  // 144-byte rows: no bank conflicts
   static constexpr int WPG = SP / 32;                   // warps per group
-  static constexpr size_t mat = 2 * (size_t)SP * KP;    // two row-chunks (M, dM)
-  static constexpr size_t vec = (size_t)CT * KC;        // the patterns' vector chunk
+  static constexpr size_t stage = 2 * (size_t)SP * KP;  // one buffer: row-chunks of M, dM
+  static constexpr size_t mat = ST * stage;
+  static constexpr size_t vec = (size_t)ST * CT * KC;   // the patterns' vector chunks
   static constexpr size_t uw = 2 * (size_t)CT * SP;     // U, W (pre-order)
   static constexpr size_t red = (size_t)CT * WPG * 3;   // per-pattern partial sums
   static size_t bytes(bool pre) { return (mat + vec + (pre ? uw : 0) + red) * sizeof(T); }
-  static_assert((size_t)KC * SP <= mat, "column chunk fits in the row-chunk buffer");
+  static_assert((size_t)KC * SP <= stage, "column chunk fits in a row-chunk buffer");
+  static_assert(SP % KC == 0, "whole chunks");
   static_assert(CT % G == 0 && SP % 32 == 0, "tile shape");
 };
 
@@ -122,27 +127,39 @@ __device__ __forceinline__ void big_row_mv(const LevelArgs<T>& a, const BigChild
     }
     return;
   }
-  T* sM = smat;
-  T* sD = smat + (size_t)SP * KP;
-  for (int t0 = 0; t0 < SP; t0 += KC) {
-    __syncthreads();  // the previous chunk has been read
+  constexpr int ST = PL::ST, NCH = SP / KC;
+  // chunk k -> buffer b: per-thread asynchronous copies, one commit group
+  auto issue = [&](int k, int b) {
+    const int t0 = k * KC;
+    T* sM = smat + (size_t)b * PL::stage;
+    T* sD = sM + (size_t)SP * KP;
     for (int i = threadIdx.x; i < SP * (KC / VN); i += kBigThreads) {
       const int row = i / (KC / VN), cv = i % (KC / VN);
-      const V m = *reinterpret_cast<const V*>(M + (size_t)row * SP + t0 + cv * VN);
-      *reinterpret_cast<V*>(sM + (size_t)row * KP + cv * VN) = m;
-      if (WITH_D) {
-        const V d = *reinterpret_cast<const V*>(dM + (size_t)row * SP + t0 + cv * VN);
-        *reinterpret_cast<V*>(sD + (size_t)row * KP + cv * VN) = d;
-      }
+      cp_async16(sM + (size_t)row * KP + cv * VN, M + (size_t)row * SP + t0 + cv * VN);
+      if (WITH_D) cp_async16(sD + (size_t)row * KP + cv * VN, dM + (size_t)row * SP + t0 + cv * VN);
     }
+    T* sv = svec + (size_t)b * CT * KC;
     for (int i = threadIdx.x; i < CT * (KC / VN); i += kBigThreads) {
       const int j = i / (KC / VN), cv = i % (KC / VN);
-      V v;
-      if (j < nvalid) v = *reinterpret_cast<const V*>(x.src + (size_t)j * x.stride + t0 + cv * VN);
-      else v = V{};
-      *reinterpret_cast<V*>(svec + j * KC + cv * VN) = v;
+      if (j < nvalid) cp_async16(sv + j * KC + cv * VN, x.src + (size_t)j * x.stride + t0 + cv * VN);
+      else *reinterpret_cast<V*>(sv + j * KC + cv * VN) = V{};
     }
-    __syncthreads();
+    cp_async_commit();
+  };
+  __syncthreads();  // the buffers' previous readers are done
+  issue(0, 0);
+  for (int k = 0; k < NCH; ++k) {
+    if (ST > 1 && k + 1 < NCH) {
+      issue(k + 1, (k + 1) % ST);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();  // every thread's copies of chunk k have landed
+    const int b = ST > 1 ? k % ST : 0;
+    const T* sM = smat + (size_t)b * PL::stage;
+    const T* sD = sM + (size_t)SP * KP;
+    const T* sv = svec + (size_t)b * CT * KC;
 #pragma unroll 2
     for (int tt = 0; tt < KC; tt += VN) {
       const V m = *reinterpret_cast<const V*>(sM + (size_t)s * KP + tt);
@@ -150,11 +167,13 @@ __device__ __forceinline__ void big_row_mv(const LevelArgs<T>& a, const BigChild
       if (WITH_D) d = *reinterpret_cast<const V*>(sD + (size_t)s * KP + tt);
 #pragma unroll
       for (int jj = 0; jj < CPG; ++jj) {
-        const V v = *reinterpret_cast<const V*>(svec + (g * CPG + jj) * KC + tt);
+        const V v = *reinterpret_cast<const V*>(sv + (g * CPG + jj) * KC + tt);
         u[jj] = big_dot(m, v, u[jj]);
         if (WITH_D) w[jj] = big_dot(d, v, w[jj]);
       }
     }
+    __syncthreads();  // chunk k's buffer may be refilled
+    if (ST == 1 && k + 1 < NCH) issue(k + 1, 0);
   }
 }
 
@@ -167,22 +186,37 @@ __device__ __forceinline__ void big_col_mv(const T* __restrict__ M, const T* A, 
   constexpr int CPG = PL::CPG, KC = PL::KC;
   using V = typename BigVec<T, T>::type;
   constexpr int VN = BigVec<T, T>::n;
+  constexpr int ST = PL::ST, NCH = SP / KC;
 #pragma unroll
   for (int jj = 0; jj < CPG; ++jj) q[jj] = T(0);
-  for (int s0 = 0; s0 < SP; s0 += KC) {
-    __syncthreads();
+  auto issue = [&](int k, int b) {
+    T* sb = smat + (size_t)b * PL::stage;
     for (int i = threadIdx.x; i < KC * (SP / VN); i += kBigThreads) {
       const int row = i / (SP / VN), cv = i % (SP / VN);
-      *reinterpret_cast<V*>(smat + (size_t)row * SP + cv * VN) =
-          *reinterpret_cast<const V*>(M + (size_t)(s0 + row) * SP + cv * VN);
+      cp_async16(sb + (size_t)row * SP + cv * VN, M + (size_t)(k * KC + row) * SP + cv * VN);
+    }
+    cp_async_commit();
+  };
+  __syncthreads();
+  issue(0, 0);
+  for (int k = 0; k < NCH; ++k) {
+    if (ST > 1 && k + 1 < NCH) {
+      issue(k + 1, (k + 1) % ST);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
     }
     __syncthreads();
+    const T* sb = smat + (size_t)(ST > 1 ? k % ST : 0) * PL::stage;
+    const int s0 = k * KC;
 #pragma unroll 4
     for (int ss = 0; ss < KC; ++ss) {
-      const T m = smat[(size_t)ss * SP + s];
+      const T m = sb[(size_t)ss * SP + s];
 #pragma unroll
       for (int jj = 0; jj < CPG; ++jj) q[jj] = fma(m, A[(size_t)(g * CPG + jj) * SP + s0 + ss], q[jj]);
     }
+    __syncthreads();
+    if (ST == 1 && k + 1 < NCH) issue(k + 1, 0);
   }
 }
 

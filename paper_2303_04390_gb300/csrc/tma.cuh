@@ -58,6 +58,24 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src,
       : "memory");
 }
 
+// Per-thread asynchronous 16-byte copy global -> shared (cached in L2
+// only); both addresses 16-byte aligned.  Copies are grouped by
+// cp_async_commit; cp_async_wait<N> returns once at most N of the thread's
+// groups are still in flight, and makes the completed ones visible to the
+// thread (a barrier then makes them visible to the block).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Programmatic dependent launch: wait until the kernel before this one in
 // the stream has completed with its writes visible, then let the kernel
 // after this one start launching its CTAs (they wait the same way before
