@@ -109,6 +109,33 @@ __device__ __forceinline__ void matvec_t(const T* __restrict__ M,
   }
 }
 
+// FP32 with 20 padded states reads its matrices in the transposed layout
+// (uses_tr_layout) and forms every product on the packed FP32 FMA.
+template <typename T, int SP>
+constexpr bool kTrSmall = std::is_same<T, float>::value && SP == 20;
+
+// out[j] = sum_i y[i] X[i][j], two outputs per packed FMA, i in order (the
+// same operations as matvec / matvec_t): X = M' gives M v, X = M gives M' a.
+template <int SP>
+__device__ __forceinline__ void rowcomb2(const float* __restrict__ X, const float (&y)[SP],
+                                         float (&out)[SP]) {
+  float2 acc[SP / 2];
+#pragma unroll
+  for (int p = 0; p < SP / 2; ++p) acc[p] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < SP; ++i) {
+    const float2 yi = make_float2(y[i], y[i]);
+    const float2* row = reinterpret_cast<const float2*>(X + i * SP);
+#pragma unroll
+    for (int p = 0; p < SP / 2; ++p) acc[p] = __ffma2_rn(row[p], yi, acc[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < SP / 2; ++p) {
+    out[2 * p] = acc[p].x;
+    out[2 * p + 1] = acc[p].y;
+  }
+}
+
 // Max |v| over this lane's states, then over the RP lanes of one pattern.
 template <typename T, int SP, int RP>
 __device__ __forceinline__ T pattern_max(const T (&v)[SP], bool active) {
@@ -275,8 +302,8 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
   __syncthreads();
   T* P = static_cast<T*>(a.P);
   T* dP = static_cast<T*>(a.dP);
-  // FP32 with 4 states: per branch [P' | dP' | P] of every category
-  constexpr bool kP4 = SP == 4 && std::is_same<T, float>::value;
+  // FP32 with 4 or 20 padded states: per branch [P' | dP' | P] of every category
+  constexpr bool kP4 = (SP == 4 || SP == 20) && std::is_same<T, float>::value;
   for (int idx = threadIdx.x; idx < UPB * SP * SP; idx += blockDim.x) {
     const int u = idx / (SP * SP), e = idx % (SP * SP);
     const int unit = unit0 + u;
@@ -293,10 +320,10 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
     }
     if constexpr (kP4) {
       const int b = unit / R, r = unit % R;
-      T* base = P + (size_t)b * kP4MatKinds * R * 16;
-      base[r * 16 + t * 4 + s] = (T)acc;
-      base[(R + r) * 16 + t * 4 + s] = (T)dacc;
-      base[(2 * R + r) * 16 + e] = (T)acc;
+      T* base = P + (size_t)b * kP4MatKinds * R * SP * SP;
+      base[(size_t)r * SP * SP + t * SP + s] = (T)acc;
+      base[(size_t)(R + r) * SP * SP + t * SP + s] = (T)dacc;
+      base[(size_t)(2 * R + r) * SP * SP + e] = (T)acc;
     } else {
       P[(size_t)unit * SP * SP + e] = (T)acc;
       dP[(size_t)unit * SP * SP + e] = (T)dacc;
@@ -343,12 +370,36 @@ __device__ __forceinline__ void load_child(const LevelArgs<T>& a, int b,
 }
 
 // u = M v (a compact state picks column y of M; the gap code gives the
-// all-ones vector), and with WITH_D also w = dM v (0 for a gap).
+// all-ones vector), and with WITH_D also w = dM v (0 for a gap).  With the
+// transposed layout (kTrSmall) M and dM hold M' and dM'.
 template <typename T, int SP, bool WITH_D>
 __device__ __forceinline__ void child_apply(const ChildIn<T, SP>& in, int S,
                                             const T* __restrict__ M,
                                             const T* __restrict__ dM,
                                             T (&u)[SP], T (&w)[SP]) {
+  if constexpr (kTrSmall<T, SP>) {
+    if (in.y >= 0) {
+      if (in.y < S) {  // column y of M = row y of M'
+#pragma unroll
+        for (int s = 0; s < SP; ++s) u[s] = M[in.y * SP + s];
+        if constexpr (WITH_D) {
+#pragma unroll
+          for (int s = 0; s < SP; ++s) w[s] = dM[in.y * SP + s];
+        }
+      } else {
+#pragma unroll
+        for (int s = 0; s < SP; ++s) u[s] = s < S ? T(1) : T(0);
+        if constexpr (WITH_D) {
+#pragma unroll
+          for (int s = 0; s < SP; ++s) w[s] = T(0);
+        }
+      }
+      return;
+    }
+    rowcomb2<SP>(M, in.v, u);
+    if constexpr (WITH_D) rowcomb2<SP>(dM, in.v, w);
+    return;
+  }
   if (in.y >= 0) {
     if (in.y < S) {
 #pragma unroll
@@ -371,20 +422,27 @@ __device__ __forceinline__ void child_apply(const ChildIn<T, SP>& in, int S,
   if constexpr (WITH_D) matvec<T, SP>(dM, in.v, w);
 }
 
-// Thread 0: copy the matrix blocks [b][r][SP][SP] of the listed branches
-// into shared slots [slot][r] of stride MS (16-byte aligned), one bulk copy
-// per (branch, category), all completing on `bar`.
+// Thread 0: copy the matrix blocks of the listed branches into shared
+// slots [slot][r] of stride MS (16-byte aligned), one bulk copy per (branch,
+// category), all completing on `bar`.  A branch holds `kinds` matrices of
+// every category ([b][kind][r][SP][SP]); `kind` selects one.
 template <typename T, int SP, int RP>
 __device__ __forceinline__ void issue_mats(const T* __restrict__ base,
                                            const int* branches, int n_br,
-                                           int R, T* dst, uint64_t* bar) {
+                                           int R, T* dst, uint64_t* bar,
+                                           int kinds = 1, int kind = 0) {
   constexpr int MS = MatStride<T, SP>::v;
   constexpr uint32_t bytes = SP * SP * sizeof(T);
   for (int i = 0; i < n_br; ++i)
     for (int q = 0; q < R; ++q)
       bulk_g2s(dst + ((size_t)i * RP + q) * MS,
-               base + ((size_t)branches[i] * R + q) * SP * SP, bytes, bar);
+               base + (((size_t)branches[i] * kinds + kind) * R + q) * SP * SP, bytes, bar);
 }
+
+// Matrix slots per node of the pre-order register kernels: P_i, P_j, dP_i,
+// dP_j, or with the transposed layout P'_i, P'_j, dP'_i, dP'_j, P_i, P_j.
+template <typename T, int SP>
+constexpr int kPreSlots = kTrSmall<T, SP> ? 6 : 4;
 
 constexpr int kDescCompactX = kDescFlagCompact0, kDescCompactY = kDescFlagCompact1;
 
@@ -425,7 +483,8 @@ post_small_kernel(LevelArgs<T> a) {
     int br[2 * NPT];
     for (int u = 0; u < nn; ++u) { br[2 * u] = d[u].y; br[2 * u + 1] = d[u].z; }
     mbar_expect_tx(&bar, (uint32_t)(2 * nn * R * SP * SP * sizeof(T)));
-    issue_mats<T, SP, RP>(a.P, br, 2 * nn, R, mats, &bar);
+    // (transposed layout: P' is kind 0 of each branch)
+    issue_mats<T, SP, RP>(a.P, br, 2 * nn, R, mats, &bar, kTrSmall<T, SP> ? kP4MatKinds : 1, 0);
   }
   ChildIn<T, SP> in[NPT][2];
 #pragma unroll
@@ -489,7 +548,8 @@ pre_small_kernel(LevelArgs<T> a) {
   constexpr int NT = kSmallThreads, CT = NT / RP;
   constexpr int MS = MatStride<T, SP>::v;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* mats = reinterpret_cast<T*>(smraw);  // [NPT][P_i, P_j, dP_i, dP_j][RP][MS]
+  constexpr int NS = kPreSlots<T, SP>;
+  T* mats = reinterpret_cast<T*>(smraw);  // [NPT][NS][RP][MS]
   __shared__ uint64_t bar;
   __shared__ typename Acc<T>::type red[NT / 32][2];
   const int g0 = blockIdx.y * NPT;
@@ -509,12 +569,19 @@ pre_small_kernel(LevelArgs<T> a) {
     d[u] = u < nn ? a.level_desc[g0 + u] : make_int4(0, 0, 0, 0);
   if (threadIdx.x == 0) {
     int br[2 * NPT];
-    mbar_expect_tx(&bar, (uint32_t)(4 * nn * R * SP * SP * sizeof(T)));
+    mbar_expect_tx(&bar, (uint32_t)(NS * nn * R * SP * SP * sizeof(T)));
     for (int u = 0; u < nn; ++u) {
       br[0] = d[u].y;
       br[1] = d[u].z;
-      issue_mats<T, SP, RP>(a.P, br, 2, R, mats + (size_t)(4 * u) * RP * MS, &bar);
-      issue_mats<T, SP, RP>(a.dP, br, 2, R, mats + (size_t)(4 * u + 2) * RP * MS, &bar);
+      T* slots = mats + (size_t)(NS * u) * RP * MS;
+      if constexpr (kTrSmall<T, SP>) {
+        for (int kind = 0; kind < kP4MatKinds; ++kind)
+          issue_mats<T, SP, RP>(a.P, br, 2, R, slots + (size_t)(2 * kind) * RP * MS, &bar,
+                                kP4MatKinds, kind);
+      } else {
+        issue_mats<T, SP, RP>(a.P, br, 2, R, slots, &bar);
+        issue_mats<T, SP, RP>(a.dP, br, 2, R, slots + (size_t)2 * RP * MS, &bar);
+      }
     }
   }
   T q[NPT][SP];
@@ -545,10 +612,13 @@ pre_small_kernel(LevelArgs<T> a) {
   for (int u = 0; u < NPT; ++u) {
     if (u >= nn) break;
     const int bi = d[u].y, bj = d[u].z;
-    const T* Pi = mats + ((4 * u) * RP + rr) * MS;
-    const T* Pj = mats + ((4 * u + 1) * RP + rr) * MS;
-    const T* Di = mats + ((4 * u + 2) * RP + rr) * MS;
-    const T* Dj = mats + ((4 * u + 3) * RP + rr) * MS;
+    const T* Pi = mats + ((NS * u) * RP + rr) * MS;  // (transposed layout: P'_i)
+    const T* Pj = mats + ((NS * u + 1) * RP + rr) * MS;
+    const T* Di = mats + ((NS * u + 2) * RP + rr) * MS;
+    const T* Dj = mats + ((NS * u + 3) * RP + rr) * MS;
+    // the rows of P_i, P_j for Eq. 4
+    const T* Ri = kTrSmall<T, SP> ? mats + ((NS * u + 4) * RP + rr) * MS : Pi;
+    const T* Rj = kTrSmall<T, SP> ? mats + ((NS * u + 5) * RP + rr) * MS : Pj;
     T ui[SP], vi[SP], uj[SP], vj[SP];
     child_apply<T, SP, true>(in[u][0], a.n_states, Pi, Di, ui, vi);
     child_apply<T, SP, true>(in[u][1], a.n_states, Pj, Dj, uj, vj);
@@ -581,7 +651,8 @@ pre_small_kernel(LevelArgs<T> a) {
       T av[SP], out[SP];
 #pragma unroll
       for (int s = 0; s < SP; ++s) av[s] = q[u][s] * uj[s];
-      matvec_t<T, SP>(Pi, av, out);
+      if constexpr (kTrSmall<T, SP>) rowcomb2<SP>(Ri, av, out);
+      else matvec_t<T, SP>(Ri, av, out);
       const T m = pattern_max<T, SP, RP>(out, active);
       rescale<T, SP>(out, m, valid_c, a.err);
       if (active)
@@ -591,7 +662,8 @@ pre_small_kernel(LevelArgs<T> a) {
       T av[SP], out[SP];
 #pragma unroll
       for (int s = 0; s < SP; ++s) av[s] = q[u][s] * ui[s];
-      matvec_t<T, SP>(Pj, av, out);
+      if constexpr (kTrSmall<T, SP>) rowcomb2<SP>(Rj, av, out);
+      else matvec_t<T, SP>(Rj, av, out);
       const T m = pattern_max<T, SP, RP>(out, active);
       rescale<T, SP>(out, m, valid_c, a.err);
       if (active)
@@ -981,7 +1053,7 @@ struct SmallNpt {
 
 template <typename T, int SP, int RP, int NPT>
 constexpr size_t small_smem(bool post) {
-  return (size_t)NPT * (post ? 2 : 4) * RP * MatStride<T, SP>::v * sizeof(T);
+  return (size_t)NPT * (post ? 2 : kPreSlots<T, SP>) * RP * MatStride<T, SP>::v * sizeof(T);
 }
 
 template <typename T, int SP, int RP>

@@ -78,7 +78,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   const size_t n_int = (size_t)N - 1;
   size_t mat, part, tmp, tmp2;
   const bool tc = uses_tensor_cores(L.SP, prec == PHYLO_FP64);
-  const bool p4 = uses_p4_layout(L.SP, prec == PHYLO_FP64);
+  const bool p4 = uses_tr_layout(L.SP, prec == PHYLO_FP64);
   const size_t unit = tc ? kTcUnitBytes
                          : (size_t)L.SP * L.SP * L.elem * (p4 ? kP4MatKinds : 1);
   if (!mul_ok(n_br * R, unit, &mat)) return "size overflow";

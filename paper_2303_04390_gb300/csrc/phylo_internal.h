@@ -58,11 +58,12 @@ constexpr int kMaxStates = 256;
 #define PHYLO_P4_TILE 64
 #endif
 constexpr int kP4TilePatterns = PHYLO_P4_TILE;
-// Their matrices are built in the orientations the products read, so no
-// kernel transposes them: per branch, [P' of every category][dP' of every
-// category][P of every category] (16 floats each; P' rows are the columns of
-// P).  The dP region is then empty.
-inline bool uses_p4_layout(int SP, bool fp64) { return SP == 4 && !fp64; }
+// The FP32 kernels for 4 and 20 padded states read their matrices in the
+// orientations the products use, built that way by the matrix kernel: per
+// branch, [P' of every category][dP' of every category][P of every
+// category] (SP x SP floats each; P' rows are the columns of P).  The dP
+// region is then empty.
+inline bool uses_tr_layout(int SP, bool fp64) { return (SP == 4 || SP == 20) && !fp64; }
 constexpr int kP4MatKinds = 3;
 
 // FP32 with 21..64 states runs on the tensor cores (kernels_tc64.cuh):

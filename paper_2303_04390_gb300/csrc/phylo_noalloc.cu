@@ -79,7 +79,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   L.n_tiles = (C + ct - 1) / ct;
   const size_t n_nodes = 2 * (size_t)N - 1, n_br = 2 * (size_t)N - 2, n_int = (size_t)N - 1;
   const bool tc = uses_tensor_cores(L.SP, false);
-  const bool p4 = uses_p4_layout(L.SP, false);
+  const bool p4 = uses_tr_layout(L.SP, false);
   const size_t mat = n_br * R * (tc ? kTcUnitBytes
                                     : L.SP * L.SP * sizeof(float) * (p4 ? kP4MatKinds : 1));
   const size_t part = n_int * (size_t)C * R * L.SP * sizeof(float);
