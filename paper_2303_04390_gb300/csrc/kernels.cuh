@@ -267,8 +267,9 @@ __device__ __forceinline__ void block_sum2(double& a, double& b,
 // ---------------------------------------------------------------------------
 // Eq. 1: P^(r)(t_b) = V diag(e^{lambda gamma_r t_b}) Vinv and
 //        dP/dt       = V diag(gamma_r lambda e^{lambda gamma_r t_b}) Vinv,
-// for every (branch, category) in one launch, computed in FP64 and stored
-// as T with zero padding.  P is formed as I + V diag(expm1(.)) Vinv: the
+// for every (branch, category) in one launch, computed and stored in FP64
+// with zero padding (the FP64 path; the FP32 paths build their matrices in
+// double-float arithmetic).  P is formed as I + V diag(expm1(.)) Vinv: the
 // direct form cancels catastrophically in the off-diagonal entries of short
 // branches (relative error ~ u |V||Vinv| / (gamma t |Q|)), and at t = 0 it
 // gives P = I exactly.
@@ -302,8 +303,6 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
   __syncthreads();
   T* P = static_cast<T*>(a.P);
   T* dP = static_cast<T*>(a.dP);
-  // FP32 with 4 or 20 padded states: per branch [P' | dP' | P] of every category
-  constexpr bool kP4 = (SP == 4 || SP == 20) && std::is_same<T, float>::value;
   for (int idx = threadIdx.x; idx < UPB * SP * SP; idx += blockDim.x) {
     const int u = idx / (SP * SP), e = idx % (SP * SP);
     const int unit = unit0 + u;
@@ -318,16 +317,8 @@ __global__ void __launch_bounds__(256) pmat_kernel(PmatArgs a) {
       }
       if (s == t) acc += 1.0;  // P = I + V diag(e^x - 1) Vinv
     }
-    if constexpr (kP4) {
-      const int b = unit / R, r = unit % R;
-      T* base = P + (size_t)b * kP4MatKinds * R * SP * SP;
-      base[(size_t)r * SP * SP + t * SP + s] = (T)acc;
-      base[(size_t)(R + r) * SP * SP + t * SP + s] = (T)dacc;
-      base[(size_t)(2 * R + r) * SP * SP + e] = (T)acc;
-    } else {
-      P[(size_t)unit * SP * SP + e] = (T)acc;
-      dP[(size_t)unit * SP * SP + e] = (T)dacc;
-    }
+    P[(size_t)unit * SP * SP + e] = (T)acc;
+    dP[(size_t)unit * SP * SP + e] = (T)dacc;
   }
 }
 
@@ -1156,12 +1147,18 @@ cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
   const int units = a.n_branches * a.n_cat;
   if (units <= 0) return cudaSuccess;
   switch (SP) {
-    case 4: {
-      constexpr int UPB = 256 / 16;
-      pmat_kernel<T, 4><<<(units + UPB - 1) / UPB, 256, 0, st>>>(a);
+    case 4:
+      if constexpr (std::is_same<T, float>::value) {
+        return launch_pmat_df_small<4>(a, st);
+      } else {
+        constexpr int UPB = 256 / 16;
+        pmat_kernel<T, 4><<<(units + UPB - 1) / UPB, 256, 0, st>>>(a);
+      }
       break;
-    }
-    case 20: pmat_kernel<T, 20><<<units, 256, 0, st>>>(a); break;
+    case 20:
+      if constexpr (std::is_same<T, float>::value) return launch_pmat_df_small<20>(a, st);
+      else pmat_kernel<T, 20><<<units, 256, 0, st>>>(a);
+      break;
     case 64:
       if constexpr (std::is_same<T, float>::value) return launch_pmat_tc64(a, st);
       else pmat_kernel<T, 64><<<units, 256, 0, st>>>(a);

@@ -615,3 +615,76 @@ cudaError_t launch_pmat_big(const PmatArgs& a, cudaStream_t st) {
 }
 
 }  // namespace phylo
+
+namespace phylo {
+
+// ---------------------------------------------------------------------------
+// Transition matrices for 4 and 20 padded states on the FP32 path (Eq. 1),
+// in the same double-float arithmetic, written in the transposed layout
+// those kernels read ([P' | dP' | P] per branch).  A block takes UPB
+// (branch, category) units; each thread owns entries (s, t) of a unit.
+// ---------------------------------------------------------------------------
+template <int SP>
+__global__ void __launch_bounds__(256) pmat_df_small_kernel(PmatArgs a) {
+  constexpr int SQ = SP * SP;
+  constexpr int UPB = (256 / SQ) > 0 ? 256 / SQ : 1;
+  __shared__ float vt_h[SQ], vt_l[SQ], vi_h[SQ], vi_l[SQ];  // V' [m][s], Vinv [m][t]
+  __shared__ DF se[UPB][SP], sd[UPB][SP];
+  const int S = a.n_states, R = a.n_cat, n_units = a.n_branches * R;
+  const int unit0 = blockIdx.x * UPB;
+  for (int i = threadIdx.x; i < SQ; i += blockDim.x) {
+    vt_h[i] = a.vsplit[i];
+    vt_l[i] = a.vsplit[SQ + i];
+    vi_h[i] = a.vsplit[2 * SQ + i];
+    vi_l[i] = a.vsplit[3 * SQ + i];
+  }
+  for (int i = threadIdx.x; i < UPB * SP; i += blockDim.x) {
+    const int u = i / SP, m = i % SP, unit = unit0 + u;
+    double e = 0.0, de = 0.0;
+    if (unit < n_units && m < S) {
+      const int b = unit / R, r = unit % R;
+      double t = a.t[b];
+      if (!(t >= 0.0) || !isfinite(t)) {
+        if (m == 0 && r == 0) atomicOr(a.err, ERR_BAD_LENGTH);
+        t = 0.0;
+      }
+      const double g = a.rates[r];
+      const double x = a.lambda[m] * g * t;
+      e = expm1(x);
+      de = g * a.lambda[m] * exp(x);
+    }
+    se[u][m] = df_from(e);
+    sd[u][m] = df_from(de);
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < UPB * SQ; idx += blockDim.x) {
+    const int u = idx / SQ, e = idx % SQ, unit = unit0 + u;
+    if (unit >= n_units) continue;
+    const int s = e / SP, t = e % SP;
+    DF ap = {0.f, 0.f}, ad = {0.f, 0.f};
+    if (s < S && t < S) {
+      for (int m = 0; m < S; ++m) {
+        const DF v = {vt_h[m * SP + s], vt_l[m * SP + s]};
+        const DF w = {vi_h[m * SP + t], vi_l[m * SP + t]};
+        df_fma(ap, df_mul(v, se[u][m]), w);
+        df_fma(ad, df_mul(v, sd[u][m]), w);
+      }
+    }
+    const float p = df_round(ap, s == t && s < S), dp = df_round(ad, false);
+    const int b = unit / R, r = unit % R;
+    float* base = static_cast<float*>(a.P) + (size_t)b * kP4MatKinds * R * SQ;
+    base[(size_t)r * SQ + t * SP + s] = p;
+    base[(size_t)(R + r) * SQ + t * SP + s] = dp;
+    base[(size_t)(2 * R + r) * SQ + e] = p;
+  }
+}
+
+template <int SP>
+cudaError_t launch_pmat_df_small(const PmatArgs& a, cudaStream_t st) {
+  constexpr int UPB = (256 / (SP * SP)) > 0 ? 256 / (SP * SP) : 1;
+  const long long units = (long long)a.n_branches * a.n_cat;
+  pmat_df_small_kernel<SP><<<(unsigned)((units + UPB - 1) / UPB), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace phylo

@@ -109,8 +109,8 @@ inline bool build_eigen_split(int S, int SP, const double* V, const double* Vinv
   }
   return reversible;
 }
-// FP32 paths whose matrix build uses the double-float tables.
-inline bool uses_eigen_split(int SP, bool fp64) { return !fp64 && SP >= 64; }
+// FP32 paths build their matrices from the double-float tables.
+inline bool uses_eigen_split(int SP, bool fp64) { return !fp64; }
 
 // Exponent planes per node: R on the tensor-core path, else 1 (one
 // exponent per (node, pattern) shared by all categories).

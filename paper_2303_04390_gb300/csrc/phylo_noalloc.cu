@@ -102,7 +102,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
   na_add(L, L.Vinv, (size_t)S * S * 8);
-  if (tc) na_add(L, L.vsplit, kEigenSplitFloats * sizeof(float));
+  na_add(L, L.vsplit, eigen_split_floats(L.SP) * sizeof(float));  // FP32: always
   na_add(L, L.lambda, (size_t)S * 8);
   na_add(L, L.pi, (size_t)S * 8);
   na_add(L, L.rates, (size_t)R * 8);
@@ -306,8 +306,8 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   static thread_local float vsplit[kEigenSplitFloats];
   bool reversible = false;
   if (L.vsplit.bytes) {
-    reversible = build_eigen_split(S, 64, V, Vinv, root_freqs, vsplit);
-    NA_TRY(up(L.vsplit, vsplit, sizeof(vsplit)), "upload V split");
+    reversible = build_eigen_split(S, L.SP, V, Vinv, root_freqs, vsplit);
+    NA_TRY(up(L.vsplit, vsplit, eigen_split_floats(L.SP) * sizeof(float)), "upload V split");
   }
   NA_TRY(up(L.lambda, lambda, (size_t)S * 8), "upload lambda");
   NA_TRY(up(L.pi, root_freqs, (size_t)S * 8), "upload pi");
