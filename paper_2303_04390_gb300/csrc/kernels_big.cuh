@@ -5,14 +5,16 @@
 // Markov-modulated codon model (Results) and 256-state models (Discussion).
 //
 // A block takes a tile of CT patterns of one node and loops over the rate
-// categories.  Thread (g, s) owns state s of the patterns g*CPG .. g*CPG +
-// CPG - 1 (G = 256 / S_pad groups of S_pad threads).  A matrix-vector
-// product streams the matrix through shared memory in chunks:
-//   u = M v   (Eq. 2, and P p, dP p of Eq. 8): chunks of KC columns, thread
-//             s reads row s of the chunk, the patterns' vector chunks are
-//             staged beside it and read as broadcasts;
-//   q = M' a  (Eq. 4): chunks of KC rows, thread t reads column t, a is read
-//             from shared memory as a broadcast.
+// categories.  Thread (g, s) owns states s, s + TPG, ... (SPT of them, TPG =
+// S_pad / SPT) of the patterns g*CPG .. g*CPG + CPG - 1 (G = 256 / TPG
+// groups).  A matrix-vector product streams the matrix through shared
+// memory in chunks, copied in by per-thread asynchronous copies into two
+// buffers so that the next chunk is in flight while one is used:
+//   u = M v   (Eq. 2, and P p, dP p of Eq. 8): chunks of KC columns; each
+//             thread reads its SPT rows of the chunk, the patterns' vector
+//             chunks are staged beside it and read as broadcasts;
+//   q = M' a  (Eq. 4): chunks of KC rows; each thread reads its SPT columns,
+//             a is read from shared memory as a broadcast.
 // Rescaling follows the other kernels: one power of two per (node, pattern)
 // shared by every category and state; the unscaled values are stored first
 // and scaled in place once the block knows the pattern's maximum (each
@@ -22,44 +24,46 @@
 namespace phylo {
 
 constexpr int kBigThreads = 256;
-// Two resident blocks for S_pad = 128 (registers capped at 128, no spills),
-// one for 256.  Measured on the 122-state workload (FP32), post- + pre-order
-// ms per evaluation: 16-pattern tiles, 32-column chunks staged through
-// registers, one block per SM: 5.8 + 11.8; 8-pattern tiles, 64-column
-// chunks, two blocks: 3.4 + 7.9; the same with asynchronous copies into two
-// 32-column buffers: 2.8 + 6.9.
+// Two resident blocks for S_pad = 128 (registers capped at 128), one for
+// 256.  Measured on the 122-state workload (FP32), post- + pre-order ms per
+// evaluation: 16-pattern tiles, 32-column chunks staged through registers,
+// one block per SM: 5.8 + 11.8; 8-pattern tiles, 64-column chunks, two
+// blocks: 3.4 + 7.9; asynchronous copies into two 32-column buffers:
+// 2.8 + 6.9; two states per thread with 16-pattern tiles: 2.2 + 5.4.
 template <int SP> constexpr int kBigMinBlocks = SP == 128 ? 2 : 1;
+
+// CT: patterns per block; KC: matrix columns (rows) per chunk; ST: chunk
+// buffers; SPT: states per thread (each matrix read then feeds SPT rows).
 template <typename T> struct BigCfg;
-// KC: matrix columns (rows) per chunk; ST: chunk buffers (2: the next
-// chunk's copies fly while the current one is used).
 template <> struct BigCfg<float> {
-  static constexpr int CT = kBigPatternsF32, KC = 32, ST = 2;
+  static constexpr int CT = kBigPatternsF32, KC = 32, ST = 2, SPT = kBigStatesPerThread;
 };
 template <> struct BigCfg<double> {
-  static constexpr int CT = kBigPatternsF64, KC = 16, ST = 2;
+  static constexpr int CT = kBigPatternsF64, KC = 16, ST = 2, SPT = 1;
 };
 
 // Shared-memory plan of one block (element counts of T).
 template <typename T, int SP>
 struct BigPlan {
   static constexpr int CT = BigCfg<T>::CT, KC = BigCfg<T>::KC, ST = BigCfg<T>::ST;
-  static constexpr int G = kBigThreads / SP, CPG = CT / G;
-  static constexpr int KP = KC + 16 / (int)sizeof(T);  // 144-byte rows: no bank conflicts
-  static constexpr int WPG = SP / 32;                   // warps per group
+  static constexpr int SPT = BigCfg<T>::SPT, TPG = SP / SPT;
+  static constexpr int G = kBigThreads / TPG, CPG = CT / G;
+  static constexpr int KP = KC + 16 / (int)sizeof(T);  // padded rows: no bank conflicts
+  static constexpr int WPG = TPG / 32;                  // warps per group
   static constexpr size_t stage = 2 * (size_t)SP * KP;  // one buffer: row-chunks of M, dM
   static constexpr size_t mat = ST * stage;
   static constexpr size_t vec = (size_t)ST * CT * KC;   // the patterns' vector chunks
   static constexpr size_t uw = 2 * (size_t)CT * SP;     // U, W (pre-order)
-  static constexpr size_t red = (size_t)CT * WPG * 3;   // per-pattern partial sums
+  static constexpr size_t red = (size_t)CT * WPG;       // per-pattern partial sums
   static size_t bytes(bool pre) { return (mat + vec + (pre ? uw : 0) + red) * sizeof(T); }
   static_assert((size_t)KC * SP <= stage, "column chunk fits in a row-chunk buffer");
-  static_assert(SP % KC == 0, "whole chunks");
-  static_assert(CT % G == 0 && SP % 32 == 0, "tile shape");
+  static_assert(SP % KC == 0 && KC % 4 == 0, "whole chunks");
+  static_assert(CT % G == 0 && TPG % 32 == 0 && CPG >= 1, "tile shape");
 };
 
-template <typename T, typename V> struct BigVec;
-template <> struct BigVec<float, float> { using type = float4; static constexpr int n = 4; };
-template <> struct BigVec<double, double> { using type = double2; static constexpr int n = 2; };
+template <typename T> struct BigVec;
+template <> struct BigVec<float> { using type = float4; static constexpr int n = 4; };
+template <> struct BigVec<double> { using type = double2; static constexpr int n = 2; };
 
 __device__ __forceinline__ float big_dot(float4 a, float4 b, float acc) {
   acc = fmaf(a.x, b.x, acc);
@@ -71,6 +75,10 @@ __device__ __forceinline__ double big_dot(double2 a, double2 b, double acc) {
   acc = fma(a.x, b.x, acc);
   return fma(a.y, b.y, acc);
 }
+__device__ __forceinline__ float big_el(float4 v, int i) {
+  return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ double big_el(double2 v, int i) { return i == 0 ? v.x : v.y; }
 
 // One child's vectors for category r: where they come from.
 template <typename T>
@@ -97,20 +105,24 @@ __device__ __forceinline__ BigChild<T> big_child(const LevelArgs<T>& a, int b, i
   return x;
 }
 
-// u[jj] = (M v_j)[s] and, with dM, w[jj] = (dM v_j)[s] for the thread's
-// patterns j = g*CPG + jj.  M, dM: global [SP][SP] (padded rows/columns 0).
-// Every thread of the block calls this (it synchronises).
+// u[i][jj] = (M v_j)[s + i*TPG] and, with dM, w[i][jj] = (dM v_j)[...] for
+// the thread's patterns j = g*CPG + jj.  M, dM: global [SP][SP] (padded
+// rows/columns 0).  Every thread of the block calls this (it synchronises).
 template <typename T, int SP, bool WITH_D>
-__device__ __forceinline__ void big_row_mv(const LevelArgs<T>& a, const BigChild<T>& x, const T* __restrict__ M,
-                           const T* __restrict__ dM, int c0, int nvalid, T* smat, T* svec,
-                           int g, int s, T (&u)[BigPlan<T, SP>::CPG],
-                           T (&w)[BigPlan<T, SP>::CPG]) {
+__device__ __forceinline__ void big_row_mv(
+    const LevelArgs<T>& a, const BigChild<T>& x, const T* __restrict__ M,
+    const T* __restrict__ dM, int c0, int nvalid, T* smat, T* svec, int g, int s,
+    T (&u)[BigPlan<T, SP>::SPT][BigPlan<T, SP>::CPG],
+    T (&w)[BigPlan<T, SP>::SPT][BigPlan<T, SP>::CPG]) {
   using PL = BigPlan<T, SP>;
-  constexpr int CPG = PL::CPG, KC = PL::KC, KP = PL::KP, CT = PL::CT;
-  using V = typename BigVec<T, T>::type;
-  constexpr int VN = BigVec<T, T>::n;
+  constexpr int CPG = PL::CPG, KC = PL::KC, KP = PL::KP, CT = PL::CT, SPT = PL::SPT,
+                TPG = PL::TPG;
+  using V = typename BigVec<T>::type;
+  constexpr int VN = BigVec<T>::n;
 #pragma unroll
-  for (int jj = 0; jj < CPG; ++jj) { u[jj] = T(0); w[jj] = T(0); }
+  for (int i = 0; i < SPT; ++i)
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) { u[i][jj] = T(0); w[i][jj] = T(0); }
   if (x.compact) {  // a column of M (gap: all ones, derivative 0)
     const int S = a.n_states;
 #pragma unroll
@@ -118,11 +130,15 @@ __device__ __forceinline__ void big_row_mv(const LevelArgs<T>& a, const BigChild
       const int j = g * CPG + jj;
       if (j >= nvalid) continue;
       const int y = a.tip_states[(size_t)x.b * a.state_stride + c0 + j];
-      if (y < S) {
-        u[jj] = M[(size_t)s * SP + y];
-        if (WITH_D) w[jj] = dM[(size_t)s * SP + y];
-      } else {
-        u[jj] = s < S ? T(1) : T(0);
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        const int si = s + i * TPG;
+        if (y < S) {
+          u[i][jj] = M[(size_t)si * SP + y];
+          if (WITH_D) w[i][jj] = dM[(size_t)si * SP + y];
+        } else {
+          u[i][jj] = si < S ? T(1) : T(0);
+        }
       }
     }
     return;
@@ -162,14 +178,21 @@ __device__ __forceinline__ void big_row_mv(const LevelArgs<T>& a, const BigChild
     const T* sv = svec + (size_t)b * CT * KC;
 #pragma unroll 2
     for (int tt = 0; tt < KC; tt += VN) {
-      const V m = *reinterpret_cast<const V*>(sM + (size_t)s * KP + tt);
-      V d{};
-      if (WITH_D) d = *reinterpret_cast<const V*>(sD + (size_t)s * KP + tt);
+      V m[SPT], d[SPT];
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        m[i] = *reinterpret_cast<const V*>(sM + (size_t)(s + i * TPG) * KP + tt);
+        d[i] = V{};
+        if (WITH_D) d[i] = *reinterpret_cast<const V*>(sD + (size_t)(s + i * TPG) * KP + tt);
+      }
 #pragma unroll
       for (int jj = 0; jj < CPG; ++jj) {
         const V v = *reinterpret_cast<const V*>(sv + (g * CPG + jj) * KC + tt);
-        u[jj] = big_dot(m, v, u[jj]);
-        if (WITH_D) w[jj] = big_dot(d, v, w[jj]);
+#pragma unroll
+        for (int i = 0; i < SPT; ++i) {
+          u[i][jj] = big_dot(m[i], v, u[i][jj]);
+          if (WITH_D) w[i][jj] = big_dot(d[i], v, w[i][jj]);
+        }
       }
     }
     __syncthreads();  // chunk k's buffer may be refilled
@@ -177,18 +200,21 @@ __device__ __forceinline__ void big_row_mv(const LevelArgs<T>& a, const BigChild
   }
 }
 
-// q[jj] = (M' a_j)[t] for t = s, a_j = A[j][*] in shared memory.  Every
+// q[i][jj] = (M' a_j)[s + i*TPG], a_j = A[j][*] in shared memory.  Every
 // thread of the block calls this (it synchronises).
 template <typename T, int SP>
-__device__ __forceinline__ void big_col_mv(const T* __restrict__ M, const T* A, T* smat, int g, int s,
-                           T (&q)[BigPlan<T, SP>::CPG]) {
+__device__ __forceinline__ void big_col_mv(const T* __restrict__ M, const T* A, T* smat, int g,
+                                           int s,
+                                           T (&q)[BigPlan<T, SP>::SPT][BigPlan<T, SP>::CPG]) {
   using PL = BigPlan<T, SP>;
-  constexpr int CPG = PL::CPG, KC = PL::KC;
-  using V = typename BigVec<T, T>::type;
-  constexpr int VN = BigVec<T, T>::n;
+  constexpr int CPG = PL::CPG, KC = PL::KC, SPT = PL::SPT, TPG = PL::TPG;
+  using V = typename BigVec<T>::type;
+  constexpr int VN = BigVec<T>::n;
   constexpr int ST = PL::ST, NCH = SP / KC;
 #pragma unroll
-  for (int jj = 0; jj < CPG; ++jj) q[jj] = T(0);
+  for (int i = 0; i < SPT; ++i)
+#pragma unroll
+    for (int jj = 0; jj < CPG; ++jj) q[i][jj] = T(0);
   auto issue = [&](int k, int b) {
     T* sb = smat + (size_t)b * PL::stage;
     for (int i = threadIdx.x; i < KC * (SP / VN); i += kBigThreads) {
@@ -209,21 +235,32 @@ __device__ __forceinline__ void big_col_mv(const T* __restrict__ M, const T* A, 
     __syncthreads();
     const T* sb = smat + (size_t)(ST > 1 ? k % ST : 0) * PL::stage;
     const int s0 = k * KC;
-#pragma unroll 4
-    for (int ss = 0; ss < KC; ++ss) {
-      const T m = sb[(size_t)ss * SP + s];
+#pragma unroll 2
+    for (int ss = 0; ss < KC; ss += VN) {
+      T m[VN][SPT];
 #pragma unroll
-      for (int jj = 0; jj < CPG; ++jj) q[jj] = fma(m, A[(size_t)(g * CPG + jj) * SP + s0 + ss], q[jj]);
+      for (int e = 0; e < VN; ++e)
+#pragma unroll
+        for (int i = 0; i < SPT; ++i) m[e][i] = sb[(size_t)(ss + e) * SP + s + i * TPG];
+#pragma unroll
+      for (int jj = 0; jj < CPG; ++jj) {
+        const V av = *reinterpret_cast<const V*>(A + (size_t)(g * CPG + jj) * SP + s0 + ss);
+#pragma unroll
+        for (int e = 0; e < VN; ++e)
+#pragma unroll
+          for (int i = 0; i < SPT; ++i) q[i][jj] = fma(m[e][i], big_el(av, e), q[i][jj]);
+      }
     }
     __syncthreads();
     if (ST == 1 && k + 1 < NCH) issue(k + 1, 0);
   }
 }
 
-// x[jj] summed (or maximised) over the S_pad threads of the group, in a
-// fixed order; every thread of the group receives the result.
+// x[jj] summed (or maximised) over the TPG threads of the group, in a fixed
+// order; every thread of the group receives the result.
 template <typename T, int SP, bool MAX>
-__device__ __forceinline__ void big_group_reduce(T (&x)[BigPlan<T, SP>::CPG], T* red, int g, int s) {
+__device__ __forceinline__ void big_group_reduce(T (&x)[BigPlan<T, SP>::CPG], T* red, int g,
+                                                 int s) {
   using PL = BigPlan<T, SP>;
   constexpr int CPG = PL::CPG, WPG = PL::WPG;
   const int lane = threadIdx.x & 31, wig = s >> 5;
@@ -254,24 +291,25 @@ template <typename T, int SP>
 __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) post_big_kernel(LevelArgs<T> a) {
   pdl_wait_and_release();
   using PL = BigPlan<T, SP>;
-  constexpr int CT = PL::CT, CPG = PL::CPG;
+  constexpr int CT = PL::CT, CPG = PL::CPG, SPT = PL::SPT, TPG = PL::TPG;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* smat = reinterpret_cast<T*>(smraw);
   T* svec = smat + PL::mat;
   T* red = svec + PL::vec;
-  __shared__ double lred[kBigThreads / SP];
+  __shared__ double lred[PL::G];
   const int k = a.level_nodes[blockIdx.y];
   const int2 ch = a.children[k];
   const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
   const int c0 = blockIdx.x * CT, nvalid = min(CT, C - c0);
-  const int s = threadIdx.x % SP, g = threadIdx.x / SP;
+  const int s = threadIdx.x % TPG, g = threadIdx.x / TPG;
   const size_t msz = (size_t)SP * SP;
-  T mx[CPG], lsum[CPG];
+  T mx[CPG], lsum[CPG], pis[SPT];
 #pragma unroll
   for (int jj = 0; jj < CPG; ++jj) { mx[jj] = T(0); lsum[jj] = T(0); }
-  const T pis = s < S ? (T)a.root_pi[s] : T(0);
+#pragma unroll
+  for (int i = 0; i < SPT; ++i) pis[i] = s + i * TPG < S ? (T)a.root_pi[s + i * TPG] : T(0);
   for (int r = 0; r < R; ++r) {
-    T ui[CPG], uj[CPG], dummy[CPG];
+    T ui[SPT][CPG], uj[SPT][CPG], dummy[SPT][CPG];
     const BigChild<T> xi = big_child(a, ch.x, c0, r, SP), xj = big_child(a, ch.y, c0, r, SP);
     big_row_mv<T, SP, false>(a, xi, a.P + ((size_t)ch.x * R + r) * msz, nullptr, c0, nvalid,
                              smat, svec, g, s, ui, dummy);
@@ -281,11 +319,14 @@ __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) post_big_kerne
 #pragma unroll
     for (int jj = 0; jj < CPG; ++jj) {
       const int j = g * CPG + jj;
-      const T p = ui[jj] * uj[jj];
-      mx[jj] = tmax(mx[jj], fabs(p));
-      if (k == a.root) lsum[jj] = fma(wr * pis, p, lsum[jj]);
-      else if (j < nvalid)
-        a.post[(((size_t)(k - a.n_tips) * C + c0 + j) * R + r) * SP + s] = p;
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        const T p = ui[i][jj] * uj[i][jj];
+        mx[jj] = tmax(mx[jj], fabs(p));
+        if (k == a.root) lsum[jj] = fma(wr * pis[i], p, lsum[jj]);
+        else if (j < nvalid)
+          a.post[(((size_t)(k - a.n_tips) * C + c0 + j) * R + r) * SP + s + i * TPG] = p;
+      }
     }
   }
   big_group_reduce<T, SP, true>(mx, red, g, s);
@@ -307,7 +348,9 @@ __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) post_big_kerne
     if (ch.y >= a.n_tips) ec += a.escale[(size_t)(ch.y - a.n_tips) * a.escale_stride + c];
     if (k != a.root) {
       T* out = a.post + (((size_t)(k - a.n_tips) * C + c) * R) * SP + s;
-      for (int r = 0; r < R; ++r) out[(size_t)r * SP] *= f;
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < SPT; ++i) out[(size_t)r * SP + i * TPG] *= f;
       if (s == 0) a.escale[(size_t)(k - a.n_tips) * a.escale_stride + c] = ec;
     } else if (s == 0) {
       // Eq. 3: L_c = sum_r w_r pi' p_root,r (scaled by f), exponents restored
@@ -331,7 +374,7 @@ template <typename T, int SP>
 __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) pre_big_kernel(LevelArgs<T> a) {
   pdl_wait_and_release();
   using PL = BigPlan<T, SP>;
-  constexpr int CT = PL::CT, CPG = PL::CPG;
+  constexpr int CT = PL::CT, CPG = PL::CPG, SPT = PL::SPT, TPG = PL::TPG;
   using A = Acc<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* smat = reinterpret_cast<T*>(smraw);
@@ -339,12 +382,12 @@ __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) pre_big_kernel
   T* U = svec + PL::vec;            // [CT][SP]: u_i, then a_i
   T* W = U + (size_t)CT * SP;       // [CT][SP]: w_i, then a_j
   T* red = W + (size_t)CT * SP;
-  __shared__ typename A::type gred[kBigThreads / SP][2];
+  __shared__ typename A::type gred[PL::G][2];
   const int k = a.level_nodes[blockIdx.y];
   const int2 ch = a.children[k];
   const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
   const int c0 = blockIdx.x * CT, nvalid = min(CT, C - c0);
-  const int s = threadIdx.x % SP, g = threadIdx.x / SP;
+  const int s = threadIdx.x % TPG, g = threadIdx.x / TPG;
   const size_t msz = (size_t)SP * SP;
   const bool int_i = ch.x >= a.n_tips, int_j = ch.y >= a.n_tips;
   T ni[CPG], nj[CPG], dd[CPG], mi[CPG], mj[CPG];
@@ -352,43 +395,53 @@ __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) pre_big_kernel
   for (int jj = 0; jj < CPG; ++jj) { ni[jj] = nj[jj] = dd[jj] = mi[jj] = mj[jj] = T(0); }
   for (int r = 0; r < R; ++r) {
     const size_t mi_off = ((size_t)ch.x * R + r) * msz, mj_off = ((size_t)ch.y * R + r) * msz;
-    T u[CPG], w[CPG];
+    T u[SPT][CPG], w[SPT][CPG];
     const BigChild<T> xi = big_child(a, ch.x, c0, r, SP), xj = big_child(a, ch.y, c0, r, SP);
     big_row_mv<T, SP, true>(a, xi, a.P + mi_off, a.dP + mi_off, c0, nvalid, smat, svec, g, s, u, w);
 #pragma unroll
-    for (int jj = 0; jj < CPG; ++jj) {
-      U[(size_t)(g * CPG + jj) * SP + s] = u[jj];
-      W[(size_t)(g * CPG + jj) * SP + s] = w[jj];
-    }
+    for (int jj = 0; jj < CPG; ++jj)
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        U[(size_t)(g * CPG + jj) * SP + s + i * TPG] = u[i][jj];
+        W[(size_t)(g * CPG + jj) * SP + s + i * TPG] = w[i][jj];
+      }
     big_row_mv<T, SP, true>(a, xj, a.P + mj_off, a.dP + mj_off, c0, nvalid, smat, svec, g, s, u, w);
     const T wr = a.cat_wt[r];
 #pragma unroll
     for (int jj = 0; jj < CPG; ++jj) {
       const int j = g * CPG + jj;
-      T q = T(0);
-      if (k == a.root) q = s < S ? (T)a.root_pi[s] : T(0);
-      else if (j < nvalid) q = a.pre[(((size_t)(k - a.n_tips) * C + c0 + j) * R + r) * SP + s];
-      const size_t o = (size_t)j * SP + s;
-      const T ui = U[o], wi = W[o];
-      const T ai = q * u[jj], aj = q * ui;  // a_i = q o P_j p_j, a_j = q o P_i p_i
-      ni[jj] = fma(wr, ai * wi, ni[jj]);
-      nj[jj] = fma(wr, aj * w[jj], nj[jj]);
-      dd[jj] = fma(wr, ai * ui, dd[jj]);
-      U[o] = ai;
-      W[o] = aj;
+#pragma unroll
+      for (int i = 0; i < SPT; ++i) {
+        const int si = s + i * TPG;
+        T q = T(0);
+        if (k == a.root) q = si < S ? (T)a.root_pi[si] : T(0);
+        else if (j < nvalid) q = a.pre[(((size_t)(k - a.n_tips) * C + c0 + j) * R + r) * SP + si];
+        const size_t o = (size_t)j * SP + si;
+        const T ui = U[o], wi = W[o];
+        const T ai = q * u[i][jj], aj = q * ui;  // a_i = q o P_j p_j, a_j = q o P_i p_i
+        ni[jj] = fma(wr, ai * wi, ni[jj]);
+        nj[jj] = fma(wr, aj * w[i][jj], nj[jj]);
+        dd[jj] = fma(wr, ai * ui, dd[jj]);
+        U[o] = ai;
+        W[o] = aj;
+      }
     }
     // Eq. 4 for internal children: q_x = P_x' a_x (unscaled for now)
     for (int x = 0; x < 2; ++x) {
       if (!(x == 0 ? int_i : int_j)) continue;
-      T q[CPG];
+      T q[SPT][CPG];
       big_col_mv<T, SP>(a.P + (x == 0 ? mi_off : mj_off), x == 0 ? U : W, smat, g, s, q);
       const int b = x == 0 ? ch.x : ch.y;
 #pragma unroll
       for (int jj = 0; jj < CPG; ++jj) {
         const int j = g * CPG + jj;
-        if (x == 0) mi[jj] = tmax(mi[jj], fabs(q[jj]));
-        else mj[jj] = tmax(mj[jj], fabs(q[jj]));
-        if (j < nvalid) a.pre[(((size_t)(b - a.n_tips) * C + c0 + j) * R + r) * SP + s] = q[jj];
+#pragma unroll
+        for (int i = 0; i < SPT; ++i) {
+          if (x == 0) mi[jj] = tmax(mi[jj], fabs(q[i][jj]));
+          else mj[jj] = tmax(mj[jj], fabs(q[i][jj]));
+          if (j < nvalid)
+            a.pre[(((size_t)(b - a.n_tips) * C + c0 + j) * R + r) * SP + s + i * TPG] = q[i][jj];
+        }
       }
     }
     __syncthreads();  // U and W are rewritten by the next category
@@ -423,7 +476,9 @@ __global__ void __launch_bounds__(kBigThreads, kBigMinBlocks<SP>) pre_big_kernel
       const T f = ldexp(T(1), -e);
       const int b = x == 0 ? ch.x : ch.y;
       T* out = a.pre + (((size_t)(b - a.n_tips) * C + c) * R) * SP + s;
-      for (int r = 0; r < R; ++r) out[(size_t)r * SP] *= f;
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int i = 0; i < SPT; ++i) out[(size_t)r * SP + i * TPG] *= f;
     }
   }
   if (s == 0) { gred[g][0] = gi; gred[g][1] = gj; }

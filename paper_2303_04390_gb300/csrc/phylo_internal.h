@@ -48,8 +48,12 @@ constexpr int kWideThreads = 256;
 constexpr int kWidePatternsF32 = 16;
 constexpr int kWidePatternsF64 = 8;
 // Patterns per block of the kernels for S_pad = 128 and 256 (kernels_big.cuh).
-constexpr int kBigPatternsF32 = 8;
+constexpr int kBigPatternsF32 = 16;
 constexpr int kBigPatternsF64 = 8;
+#ifndef PHYLO_BIG_SPT
+#define PHYLO_BIG_SPT 2
+#endif
+constexpr int kBigStatesPerThread = PHYLO_BIG_SPT;  // FP32: states per thread
 constexpr int kMaxStates = 256;
 
 // Patterns per block of the FP32 4-state kernels (kernels_p4.cuh), one
