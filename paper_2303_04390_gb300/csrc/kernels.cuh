@@ -438,16 +438,18 @@ constexpr int kPreSlots = kTrSmall<T, SP> ? 6 : 4;
 constexpr int kDescCompactX = kDescFlagCompact0, kDescCompactY = kDescFlagCompact1;
 
 // Resident blocks asked of the register allocator: the FP32 20-state
-// kernels hold three 20-element vectors per input and run latency-bound;
-// capping them at 3 blocks (168 registers) measured 12% faster on the
-// 256-taxon amino-acid workload than the unbounded 212 registers (2 blocks).
-template <typename T, int SP>
-constexpr int kSmallMinBlocks = (SP == 20 && sizeof(T) == 4) ? 3 : 0;
+// kernels hold three 20-element vectors per input and run latency-bound.
+// On the 256-taxon amino-acid workload, capping the pre-order kernel at 3
+// blocks (168 registers) measured 12% faster than the unbounded 212
+// registers (2 blocks); 4 blocks spilled and was slower.  The post-order
+// kernel runs 4% faster at 4 blocks (127 registers) than at 3.
+template <typename T, int SP, bool PRE>
+constexpr int kSmallMinBlocks = (SP == 20 && sizeof(T) == 4) ? (PRE ? 3 : 4) : 0;
 
 // Post-order level (Eq. 2): p_k = (P_i p_i) o (P_j p_j), rescaled; at the
 // root also log P(Y_c) (Eq. 3) weighted by W_c and summed per tile.
 template <typename T, int SP, int RP, int NPT>
-__global__ void __launch_bounds__(kSmallThreads, kSmallMinBlocks<T, SP>)
+__global__ void __launch_bounds__(kSmallThreads, kSmallMinBlocks<T, SP, false>)
 post_small_kernel(LevelArgs<T> a) {
   constexpr int NT = kSmallThreads, CT = NT / RP;
   constexpr int MS = MatStride<T, SP>::v;
@@ -534,7 +536,7 @@ post_small_kernel(LevelArgs<T> a) {
 // stored (rescaled) for internal children; the ratio for branches i and j
 // is reduced over the tile's patterns with weights W_c (Eq. 7).
 template <typename T, int SP, int RP, int NPT>
-__global__ void __launch_bounds__(kSmallThreads, kSmallMinBlocks<T, SP>)
+__global__ void __launch_bounds__(kSmallThreads, kSmallMinBlocks<T, SP, true>)
 pre_small_kernel(LevelArgs<T> a) {
   constexpr int NT = kSmallThreads, CT = NT / RP;
   constexpr int MS = MatStride<T, SP>::v;
