@@ -27,7 +27,10 @@
  *  - All device work is ordered on the stream given to phylo_create
  *    (NULL = the legacy default stream).
  *  - Matrices are row-major FP64.  Sizes: N tips, C patterns, S states
- *    (2 <= S <= 64), R categories (1 <= R <= 8).
+ *    (2 <= S <= 256; S <= 64 for phylo_evaluate_noalloc), R categories
+ *    (1 <= R <= 8).  Kernels by padded state count S_pad: 4 and 20 (CUDA
+ *    cores), 64 (FP32: tensor cores), 128 and 256 (CUDA cores, matrices
+ *    streamed through shared memory).
  */
 #ifndef PHYLO_API_H
 #define PHYLO_API_H
@@ -86,8 +89,10 @@ int phylo_create(phylo_ctx** ctx, int n_tips, int n_patterns, int n_states,
 int phylo_set_tree(phylo_ctx* ctx, const int32_t* parent);
 
 /* Compact tip data (Methods, gradient subsection: an observed tip is
- * stored as one integer per pattern).  states: host uint8 [N][C], values in [0, S]; S marks a gap or
- * unknown character (an all-ones partial). */
+ * stored as one integer per pattern).  states: host uint8 [N][C], values in
+ * [0, S]; S marks a gap or unknown character (an all-ones partial).  With
+ * S = 256 every byte value is a state (no gap code): gaps then go through
+ * phylo_set_tip_partials. */
 int phylo_set_tip_states(phylo_ctx* ctx, const uint8_t* states);
 
 /* Partial likelihood vector for one tip (ambiguity codes, sequencing
