@@ -1,7 +1,7 @@
 """Shared helpers for the parity tests: the oracle run (optionally over
 pattern shards in a spawn process pool) and the tolerance check.
 
-Tolerances (derivation in DESIGN.md, "Tolerances"):
+Tolerances:
   FP64 path: |logL - logL*| <= 1e-12 |logL*|;
              |g - g*| <= max(1e-12 |g*|, 1e-11 B)
   FP32 path: |logL - logL*| <= 1e-5 |logL*|;
