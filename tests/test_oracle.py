@@ -140,6 +140,31 @@ def test_two_taxon_jc69_closed_form(ncat):
         assert abs(grad[0] - (n_same * g_same + n_diff * g_diff)) < 1e-12
 
 
+def _golden_jc69():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "jc69_two_taxon.txt")
+    return [tuple(float(x) for x in line.split()) for line in open(path)
+            if line.strip() and not line.startswith("#")]
+
+
+def test_golden_jc69_two_taxon():
+    """The stored closed-form values (tests/golden/jc69_two_taxon.txt): one
+    same-state and one different-state site on a two-taxon tree with both
+    branches T/2."""
+    Q, pi = synth.jc69()
+    parent = np.array([2, 2, -1], dtype=np.int32)
+    states = np.array([[0, 0], [0, 1]], dtype=np.uint8)
+    for T, ls, dls, ld, dld in _golden_jc69():
+        if ld == 0.0:
+            continue
+        logL, grad, _ = O.evaluate(parent, np.array([T / 2, T / 2]), Q, pi, np.ones(1),
+                                   np.ones(1), np.ones(2), tip_states=states)
+        want = math.log(ls) + math.log(ld)
+        assert abs(logL - want) <= 1e-13 * abs(want)
+        g = dls / ls + dld / ld
+        np.testing.assert_allclose(grad, [g, g], rtol=1e-11, atol=1e-14)
+
+
 @pytest.mark.parametrize("n_tips,n_states,ncat", [(6, 4, 2), (5, 4, 4),
                                                    (4, 20, 2), (3, 61, 2)])
 def test_likelihood_matches_brute_force(n_tips, n_states, ncat):

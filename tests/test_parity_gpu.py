@@ -123,6 +123,34 @@ def test_empty_alignment(S, precision):
     assert logL == 0.0 and np.all(grad == 0.0)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_golden_jc69_two_taxon(precision):
+    """The CUDA path against the stored closed-form JC69 values
+    (tests/golden/jc69_two_taxon.txt), independently of the oracle."""
+    import math
+    import os
+    import paper_2303_04390_gb300 as pg
+    path = os.path.join(os.path.dirname(__file__), "golden", "jc69_two_taxon.txt")
+    rows = [tuple(float(x) for x in line.split()) for line in open(path)
+            if line.strip() and not line.startswith("#")]
+    Q, pi = synth.jc69()
+    for T, ls, dls, ld, dld in rows:
+        if ld == 0.0:
+            continue
+        w = synth.Workload("jc69-two-taxon", np.array([2, 2, -1], dtype=np.int32),
+                           np.array([T / 2, T / 2]), Q, pi, np.ones(1), np.ones(1),
+                           np.array([[0, 0], [0, 1]], dtype=np.uint8), np.ones(2), precision)
+        ctx = pg.from_workload(w, precision)
+        logL, grad = ctx.evaluate()
+        ctx.close()
+        want = math.log(ls) + math.log(ld)
+        g = dls / ls + dld / ld
+        B = abs(dls / ls) + abs(dld / ld)
+        tol = TOL[precision]
+        assert abs(logL - want) <= tol["ll_rel"] * abs(want) + 1e-300
+        assert np.all(np.abs(grad - g) <= np.maximum(tol["g_rel"] * abs(g), tol["g_cond"] * B))
+
+
 def test_single_pattern_many_tips():
     w = synth.small_workload(300, 4, 4, 1, seed=25, tree="yule")
     ref = oracle_eval(w)
