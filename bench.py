@@ -501,6 +501,19 @@ def run_ours(args):
         "launches_per_evaluation": n_launch_dom,
         "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
     }
+    if 4 < w.n_states <= 20 and precision == "fp32":
+        # 20 states sit near the FP32 ridge (about 10 flop per byte moved):
+        # the CUDA-core rate of the same phase beside the HBM figure
+        fl = algorithmic_flops(w)
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = peaks.get("sm_max_mhz") or 2070.0
+        apeak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+        aach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
+        roofline["alu"] = {"achieved": aach, "peak": apeak, "unit": "TFLOP/s",
+                           "frac": aach / apeak,
+                           "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x "
+                                        f"{mhz:.0f} MHz",
+                           "algorithmic_flops_per_launch": fl[dom] / n_launch_dom}
     if w.n_states > 64:
         # 65..256 states: the level kernels are CUDA-core contractions
         # (about 2 S flop per byte moved), so the bound is the FP32 (FP64)
