@@ -69,6 +69,9 @@ SMALL = [
     (7, 90, 3, 17, "balanced"),
     (5, 256, 2, 19, "yule"),
     (8, 200, 1, 9, "caterpillar"),
+    (5, 65, 8, 21, "yule"),            # smallest S of S_pad 128, eight categories
+    (4, 129, 3, 18, "balanced"),       # smallest S of S_pad 256
+    (30, 122, 2, 17, "caterpillar"),   # deep chain at 122 states: rescaling at every node
 ]
 
 
