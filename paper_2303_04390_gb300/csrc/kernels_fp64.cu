@@ -18,6 +18,21 @@ __global__ void __launch_bounds__(256) reduce_kernel(ReduceArgs a) {
   const double* src = warp < a.n_branches
                           ? a.gpart + (size_t)warp * a.n_tiles
                           : a.lpart;
+  if (a.gpart_pairs && warp < a.n_branches) {
+    // float-pair tile sums: summed as pairs (error-free transformations,
+    // ~48 bits), converted to FP64 once
+    const float2* s2 = reinterpret_cast<const float2*>(src);
+    F2 acc = {0.f, 0.f};
+    for (int i = lane; i < a.n_tiles; i += 32) {
+      const float2 p = s2[i];
+      acc = f2_add(acc, F2{p.x, p.y});
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      acc = f2_add(acc, F2{__shfl_xor_sync(kFull, acc.hi, o), __shfl_xor_sync(kFull, acc.lo, o)});
+    if (lane == 0) a.out[1 + warp] = (double)acc.hi + (double)acc.lo;
+    return;
+  }
   double acc = 0.0;
   for (int i = lane; i < a.n_tiles; i += 32) acc += src[i];
 #pragma unroll

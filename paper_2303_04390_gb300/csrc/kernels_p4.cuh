@@ -388,8 +388,10 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       gi = f2_add(gi, red[w][0]);
       gj = f2_add(gj, red[w][1]);
     }
-    a.gpart[(size_t)bi * a.n_tiles + blockIdx.x] = Acc<float>::to_double(gi);
-    a.gpart[(size_t)bj * a.n_tiles + blockIdx.x] = Acc<float>::to_double(gj);
+    // the pair as stored (the reduction converts to FP64: no FP64 here)
+    float2* gp = reinterpret_cast<float2*>(a.gpart);
+    gp[(size_t)bi * a.n_tiles + blockIdx.x] = make_float2(gi.hi, gi.lo);
+    gp[(size_t)bj * a.n_tiles + blockIdx.x] = make_float2(gj.hi, gj.lo);
   }
 }
 

@@ -189,9 +189,11 @@ struct PmatArgs {
 };
 
 struct ReduceArgs {
-  const double* gpart;   // [n_branches][n_tiles]
+  const double* gpart;   // [n_branches][n_tiles]; with gpart_pairs each entry
+                         // holds a float pair {hi, lo} (value hi + lo)
   const double* lpart;   // [n_tiles]
   int n_tiles, n_branches;
+  int gpart_pairs;       // the FP32 4-state kernels' tile sums (no FP64 in them)
   double* out;           // [1 + n_branches]
 };
 
