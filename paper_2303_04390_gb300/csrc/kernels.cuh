@@ -664,8 +664,15 @@ pre_small_kernel(LevelArgs<T> a) {
     }
     block_sum_acc<T, NT>(gi, gj, red, RP);
     if (threadIdx.x == 0) {
-      a.gpart[(size_t)bi * a.n_tiles + blockIdx.x] = A::to_double(gi);
-      a.gpart[(size_t)bj * a.n_tiles + blockIdx.x] = A::to_double(gj);
+      if constexpr (std::is_same<T, float>::value) {
+        // the pair as stored (the reduction converts to FP64)
+        float2* gp = reinterpret_cast<float2*>(a.gpart);
+        gp[(size_t)bi * a.n_tiles + blockIdx.x] = make_float2(gi.hi, gi.lo);
+        gp[(size_t)bj * a.n_tiles + blockIdx.x] = make_float2(gj.hi, gj.lo);
+      } else {
+        a.gpart[(size_t)bi * a.n_tiles + blockIdx.x] = A::to_double(gi);
+        a.gpart[(size_t)bj * a.n_tiles + blockIdx.x] = A::to_double(gj);
+      }
     }
     __syncthreads();  // red[] is reused by the next node
   }

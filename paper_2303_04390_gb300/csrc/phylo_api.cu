@@ -311,7 +311,7 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
   ra.lpart = ctx->dev<double>(ctx->L.lpart);
   ra.n_tiles = ctx->L.n_tiles;
   ra.n_branches = phase == kPhaseLogLOnly ? 0 : 2 * ctx->N - 2;
-  ra.gpart_pairs = ctx->precision == PHYLO_FP32 && ctx->L.SP == 4;
+  ra.gpart_pairs = ctx->precision == PHYLO_FP32 && (ctx->L.SP == 4 || ctx->L.SP == 20);
   ra.out = ctx->dev<double>(ctx->L.out);
   return launch_reduce(ra, st);
 }

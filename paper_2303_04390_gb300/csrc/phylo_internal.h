@@ -193,7 +193,8 @@ struct ReduceArgs {
                          // holds a float pair {hi, lo} (value hi + lo)
   const double* lpart;   // [n_tiles]
   int n_tiles, n_branches;
-  int gpart_pairs;       // the FP32 4-state kernels' tile sums (no FP64 in them)
+  int gpart_pairs;       // FP32 with 4 or 20 padded states: tile sums as float
+                         // pairs (no FP64 in those level kernels)
   double* out;           // [1 + n_branches]
 };
 

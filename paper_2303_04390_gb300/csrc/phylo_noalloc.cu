@@ -395,7 +395,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   ReduceArgs ra{};
   ra.gpart = a.gpart;
   ra.lpart = a.lpart;
-  ra.gpart_pairs = L.SP == 4;  // FP32 4-state kernels
+  ra.gpart_pairs = L.SP == 4 || L.SP == 20;  // FP32 4- and 20-state kernels
   ra.n_tiles = L.n_tiles;
   ra.n_branches = 2 * N - 2;
   ra.out = reinterpret_cast<double*>(ws + L.out.off);
