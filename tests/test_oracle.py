@@ -192,8 +192,9 @@ def test_pattern_probabilities_sum_to_one():
     assert abs(np.exp(ll).sum() - 1.0) < 1e-13
 
 
-def test_any_node_identity():
-    w = synth.small_workload(12, 4, 4, 40, seed=3)
+@pytest.mark.parametrize("n_tips,n_states", [(12, 4), (6, 122)])
+def test_any_node_identity(n_tips, n_states):
+    w = synth.small_workload(n_tips, n_states, 4, 40, seed=3)
     _, _, _, det = O.evaluate(w.parent, w.t, w.Q, w.pi, w.rates, w.weights,
                               w.pattern_weights, tip_states=w.tip_states,
                               return_details=True)
@@ -329,8 +330,11 @@ def _reroot(parent, t, new_child, frac):
     return new_parent, new_t
 
 
-def test_reroot_invariance():
-    w = synth.small_workload(9, 4, 4, 30, seed=12)
+@pytest.mark.parametrize("n_states", [4, 122])
+def test_reroot_invariance(n_states):
+    """Rerooting under a reversible model with root = pi (also the 122-state
+    Markov-modulated codon model)."""
+    w = synth.small_workload(9, n_states, 4 if n_states == 4 else 2, 30, seed=12)
     ll0, g0, _ = O.evaluate(w.parent, w.t, w.Q, w.pi, w.rates, w.weights,
                             w.pattern_weights, tip_states=w.tip_states)
     root = len(w.parent) - 1
