@@ -5,22 +5,31 @@ Tolerances:
   FP64 path: |logL - logL*| <= 1e-12 |logL*|;
              |g - g*| <= max(1e-12 |g*|, 1e-11 B)
   FP32 path: |logL - logL*| <= 1e-5 |logL*|;
-             |g - g*| <= max(1e-4 |g*|,  1e-5 B)
+             |g - g*| <= max(1e-4 |g*|,  1e-6 B)
 where B is the entry's conditioning scale from the oracle: the sum over
 patterns and categories of the absolute values of the Eq. 8 numerator terms
-over the denominator.  An entry that cancels across patterns or inside a
-pattern (|g*| << B) cannot be held to a bound relative to |g*| by any
-finite-precision evaluation -- two FP64 evaluations in different but exact
-orders already differ by ~1e-13 B -- so the bound falls back to a fraction
-of B.  For FP64 that fraction is 1e-11: the eigen route of Eq. 1 leaves an
-absolute error of order S u sqrt(pi_max / pi_min) in the small entries of
-P (two- and three-nucleotide codon changes on short branches), which the
-61-state workload turns into ~3e-12 B; the Taylor route of the oracle does
-not share it.
+over the denominator (pinned independently by the oracle tests: a closed
+form on two taxa and a substitution route).  An entry that cancels across
+patterns or inside a pattern (|g*| << B) cannot be held to a bound relative
+to |g*| by any finite-precision evaluation -- two FP64 evaluations in
+different but exact orders already differ by ~1e-14 B -- so the bound falls
+back to a fraction of B.  FP32: the measured worst is below 1e-7 B on every
+workload, so 1e-6 B leaves a factor of ten.  FP64: the eigen route of Eq. 1
+leaves an absolute error of order S u sqrt(pi_max / pi_min) in the small
+entries of P (two- and three-nucleotide codon changes on short branches),
+which the 61-state workload turns into ~3e-12 B; the Taylor route of the
+oracle does not share it.
+
+compare() returns the figures the tests print: the relative error of log
+P(Y), the worst error over its bound, the worst relative error over the
+entries with |g*| >= 1e-3 B (those the relative bound governs), the worst
+error in units of B, and how many entries pass only through the B fallback.
 """
 from __future__ import annotations
 
+import json
 import multiprocessing as mp
+import os
 from concurrent.futures import ProcessPoolExecutor
 
 import numpy as np
@@ -29,7 +38,7 @@ from oracle import phylo_oracle as O
 
 TOL = {
     "fp64": dict(ll_rel=1e-12, g_rel=1e-12, g_cond=1e-11),
-    "fp32": dict(ll_rel=1e-5, g_rel=1e-4, g_cond=1e-5),
+    "fp32": dict(ll_rel=1e-5, g_rel=1e-4, g_cond=1e-6),
 }
 
 
@@ -68,7 +77,7 @@ def oracle_eval(w, t=None, tip_partials=None, shards=1):
 
 
 def compare(logL, grad, ref, precision, what=""):
-    """Assert the tolerances above; return (ll_rel_err, worst bound ratio)."""
+    """Assert the tolerances above; return the error figures (a dict)."""
     ll_ref, g_ref, A, B = ref
     tol = TOL[precision]
     ll_err = abs(logL - ll_ref)
@@ -76,7 +85,8 @@ def compare(logL, grad, ref, precision, what=""):
         f"{what}: logL {logL!r} vs oracle {ll_ref!r} (rel err "
         f"{ll_err / max(abs(ll_ref), 1e-300):.3e})")
     err = np.abs(np.asarray(grad) - g_ref)
-    bound = np.maximum(tol["g_rel"] * np.abs(g_ref), tol["g_cond"] * B)
+    rel_bound = tol["g_rel"] * np.abs(g_ref)
+    bound = np.maximum(rel_bound, tol["g_cond"] * B)
     ratio = np.where(bound > 0, err / np.where(bound > 0, bound, 1.0),
                      np.where(err > 0, np.inf, 0.0))
     worst = int(np.argmax(ratio)) if ratio.size else 0
@@ -84,5 +94,29 @@ def compare(logL, grad, ref, precision, what=""):
         f"{what}: gradient entry {worst}: {grad[worst]!r} vs oracle "
         f"{g_ref[worst]!r} (|err| {err[worst]:.3e}, bound {bound[worst]:.3e},"
         f" B {B[worst]:.3e}, A {A[worst]:.3e})")
-    return (ll_err / max(abs(ll_ref), 1e-300),
-            float(ratio[worst]) if ratio.size else 0.0)
+    big = np.abs(g_ref) >= 1e-3 * B
+    rel = err[big] / np.abs(g_ref[big]) if np.any(big) else np.zeros(1)
+    in_b = err / np.where(B > 0, B, 1.0)
+    stats = {
+        "ll_rel_err": ll_err / max(abs(ll_ref), 1e-300),
+        "worst_err_over_bound": float(ratio[worst]) if ratio.size else 0.0,
+        "worst_rel_err_large_entries": float(np.max(rel)),
+        "worst_err_in_B": float(np.max(in_b)) if in_b.size else 0.0,
+        "n_entries": int(err.size),
+        "n_fallback_only": int(np.sum(err > rel_bound)),
+    }
+    log = os.environ.get("PHYLO_PARITY_LOG")
+    if log:  # one JSON line per comparison, for the error tables
+        with open(log, "a") as f:
+            f.write(json.dumps({"what": what, "precision": precision,
+                                **stats}) + "\n")
+    return stats
+
+
+def describe(stats):
+    return (f"logL rel err {stats['ll_rel_err']:.2e}; gradient: worst "
+            f"err/bound {stats['worst_err_over_bound']:.3f}, worst rel err "
+            f"(|g*| >= 1e-3 B) {stats['worst_rel_err_large_entries']:.2e}, "
+            f"worst err/B {stats['worst_err_in_B']:.2e}, "
+            f"{stats['n_fallback_only']} of {stats['n_entries']} entries pass "
+            f"only through the B fallback")

@@ -481,6 +481,111 @@ def test_planted_transposed_postorder_matrix_is_caught():
     assert not np.allclose(np.exp(ll), bf, rtol=1e-6)
 
 
+def _two_taxon_jc_B(rates, weights, x, y, T):
+    """B of either branch of the two-taxon JC69 tree for one site (x, y):
+    q of branch 0 is (1/4) P(gamma T)[., y], p is the one-hot e_x, and JC69
+    has |Q[u, s]| = 1 on the diagonal and 1/3 off it, so the absolute
+    numerator is gamma (1/4) [P_xy + (1 - P_xy) / 3] and the denominator
+    (1/4) P_xy (column sums of the symmetric P are 1).  With
+    P_same = 1/4 + 3/4 e and P_diff = 1/4 - 1/4 e (e = exp(-4 gamma T / 3))
+    the bracket is P_same + P_diff (x = y) or P_diff + 1/4 + e/12 (x != y)."""
+    num = den = 0.0
+    for g, w in zip(rates, weights):
+        e = math.exp(-4.0 * g * T / 3.0)
+        p_same, p_diff = 0.25 + 0.75 * e, 0.25 - 0.25 * e
+        if x == y:
+            num += w * g * (p_same + p_diff)
+            den += w * p_same
+        else:
+            num += w * g * (p_diff + 0.25 + e / 12.0)
+            den += w * p_diff
+    return num / den
+
+
+@pytest.mark.parametrize("ncat", [1, 4])
+def test_conditioning_scale_two_taxon_closed_form(ncat):
+    """B (the sum over patterns of the Eq. 8 terms in absolute value, over
+    the denominator) of the two-taxon JC69 tree in closed form."""
+    Q, pi = synth.jc69()
+    rates, weights = synth.discrete_gamma(0.5, ncat)
+    parent = np.array([2, 2, -1], dtype=np.int32)
+    t = np.array([0.07, 0.31])
+    states = np.array([[0, 0, 1, 3, 2, 1], [0, 2, 1, 0, 2, 3]], dtype=np.uint8)
+    W = np.array([3.0, 1.0, 2.0, 5.0, 1.0, 4.0])
+    _, _, _, B = O.evaluate_with_scales(parent, t, Q, pi, rates, weights, W,
+                                        tip_states=states)
+    want = sum(W[c] * _two_taxon_jc_B(rates, weights, states[0, c],
+                                      states[1, c], t.sum())
+               for c in range(states.shape[1]))
+    np.testing.assert_allclose(B, [want, want], rtol=1e-13)
+
+
+def _scale_by_substitution(w):
+    """B_i by a second route: one pruning pass per branch with P_i replaced
+    by gamma_r P_i |Q| gives, at the root, sum_r w_r gamma_r a_i' P_i |Q| p_i
+    (= the absolute Eq. 8 numerator, since p, q >= 0 and q_i = P_i' a_i);
+    dividing by P(Y_c) and summing with the pattern weights gives B_i."""
+    Q = np.asarray(w.Q)
+    tips = O.tip_partial_vectors(Q.shape[0], w.tip_states)
+    P = O.branch_matrices(w.parent, w.t, Q, w.rates)
+    p, scale, root = O.postorder(w.parent, P, w.rates, tips)
+    base = np.log(np.einsum("rc,r->c", np.einsum("rcs,s->rc", p[root], w.pi),
+                            w.weights)) + scale[root]
+    B = np.zeros(len(w.parent) - 1)
+    for b in range(len(w.parent)):
+        if b == root:
+            continue
+        M = np.stack([g * P[b][r] @ np.abs(Q) for r, g in enumerate(w.rates)])
+        pd, sd, _ = O.postorder(w.parent, P, w.rates, tips, substitute=b, dP=M)
+        val = np.einsum("rc,r->c", np.einsum("rcs,s->rc", pd[root], w.pi),
+                        w.weights)
+        B[b] = float(np.dot(w.pattern_weights, val * np.exp(sd[root] - base)))
+    return B
+
+
+def _scale_workloads():
+    w4 = synth.small_workload(7, 4, 4, 25, seed=19, mean_t=0.2)
+    w4.Q, w4.pi = synth.hky85(4.0, np.array([0.1, 0.2, 0.3, 0.4]))
+    w4.tip_states[2, 3] = 4  # gap
+    w20 = synth.small_workload(5, 20, 2, 12, seed=20, mean_t=0.3)
+    return [w4, w20]
+
+
+def test_conditioning_scale_matches_substitution_route():
+    for w in _scale_workloads():
+        _, _, _, B = O.evaluate_with_scales(w.parent, w.t, w.Q, w.pi, w.rates,
+                                            w.weights, w.pattern_weights,
+                                            tip_states=w.tip_states)
+        np.testing.assert_allclose(B, _scale_by_substitution(w), rtol=1e-11)
+
+
+@pytest.mark.parametrize("mistake", ["times_S", "signed_Q", "abs_after_sum",
+                                     "transposed_Q"])
+def test_planted_scale_mistake_is_caught(monkeypatch, mistake):
+    """A wrong conditioning scale (which would silently widen every parity
+    bound) fails the substitution-route pin."""
+    right = O.gradient_numerator_abs
+
+    def wrong(p_i, Q, q_i, rates):
+        g = np.asarray(rates)[:, None]
+        if mistake == "times_S":
+            return right(p_i, Q, q_i, rates) * np.asarray(Q).shape[0]
+        if mistake == "signed_Q":
+            return g * np.einsum("rcs,us,rcu->rc", np.abs(p_i), Q, np.abs(q_i))
+        if mistake == "abs_after_sum":
+            return np.abs(g * np.einsum("rcs,us,rcu->rc", p_i, Q, q_i))
+        return g * np.einsum("rcs,su,rcu->rc", np.abs(p_i), np.abs(Q), np.abs(q_i))
+
+    monkeypatch.setattr(O, "gradient_numerator_abs", wrong)
+    caught = False
+    for w in _scale_workloads():
+        _, _, _, B = O.evaluate_with_scales(w.parent, w.t, w.Q, w.pi, w.rates,
+                                            w.weights, w.pattern_weights,
+                                            tip_states=w.tip_states)
+        caught |= not np.allclose(B, _scale_by_substitution(w), rtol=1e-11)
+    assert caught
+
+
 def test_conditioning_scales():
     """The conditioning scales bound the entries: B_i >= A_i >= |grad_i|."""
     w = synth.small_workload(9, 4, 4, 30, seed=18)

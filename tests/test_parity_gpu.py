@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import synth
-from parity import TOL, compare, oracle_eval
+from parity import TOL, compare, describe, oracle_eval
 
 pytestmark = pytest.mark.gpu
 
@@ -281,9 +281,8 @@ def test_full_size_workloads(name):
     for prec in sorted({precision, "fp64"}):
         ctx = pg.from_workload(w, prec)
         logL, grad = ctx.evaluate()
-        ll_err, ratio = compare(logL, grad, ref, prec, f"{name} {prec}")
-        print(f"{name} {prec}: logL rel err {ll_err:.2e}, worst gradient "
-              f"error / bound {ratio:.3f}")
+        stats = compare(logL, grad, ref, prec, f"{name} {prec}")
+        print(f"{name} {prec}: {describe(stats)}")
         # pulley principle on the device result (reversible, root = pi)
         root = 2 * w.n_tips - 2
         a, b = np.nonzero(w.parent == root)[0]
