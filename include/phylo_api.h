@@ -158,16 +158,23 @@ int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out,
                                 void* const* events);
 
 /* The evaluation split at its natural seam, for reverse-mode use (the
- * pre-order pass is the backward of the post-order pass): forward runs the
- * matrix build, the post-order pass and the log-likelihood reduction and
- * writes log P(Y) (1 FP64 value) to the device pointer `out`; backward runs
- * the pre-order pass with the fused gradient and the gradient reduction
- * and writes d log P(Y)/d t (2N-2 FP64 values) to the device pointer `out`.
- * Both are asynchronous on the stream.  Backward returns PHYLO_ESTATE
- * unless a forward (or a full evaluation) ran since the last change of the
- * branch lengths. */
-int phylo_forward_device(phylo_ctx* ctx, double* out);
-int phylo_backward_device(phylo_ctx* ctx, double* out);
+ * pre-order pass of Eq. 4 with the Eq. 8 ratio is the backward of the
+ * post-order pass of Eqs. 2-3): forward runs the matrix build, the
+ * post-order pass and the log-likelihood reduction and writes log P(Y)
+ * (1 FP64 value) to the device pointer `out`; backward runs the pre-order
+ * pass with the fused gradient and the gradient reduction and writes
+ * d log P(Y)/d t (2N-2 FP64 values) to the device pointer `out`.  Both are
+ * asynchronous on the stream.
+ *
+ * Every pass that rewrites the context's post-order partials (a forward,
+ * any evaluation) gets a new generation number; forward returns its own in
+ * *generation (may be NULL).  Backward takes the generation of the forward
+ * it differentiates and returns PHYLO_ESTATE, without launching anything,
+ * unless that forward is still the latest such pass and the branch
+ * lengths have not changed since: two forwards before one backward cannot
+ * silently return the second forward's gradient for the first. */
+int phylo_forward_device(phylo_ctx* ctx, double* out, uint64_t* generation);
+int phylo_backward_device(phylo_ctx* ctx, double* out, uint64_t generation);
 
 /* Chain-rule epilogues on the gradient of the most recent evaluation on
  * this context (phylo_evaluate, phylo_evaluate_device or
@@ -219,15 +226,29 @@ int phylo_launches_per_evaluation(const phylo_ctx* ctx);
 int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
                        int* n_pre_levels);
 
+/* Self-test of the bounded device waits (no counterpart in the paper; the
+ * kernels' asynchronous copies and MMAs complete on mbarriers, and every
+ * wait gives up after a bounded number of try_wait rounds, raising a flag
+ * that the host reports as PHYLO_ETIMEOUT).  Launches one CTA on `stream`
+ * (a cudaStream_t, NULL = legacy default) that waits, with the same
+ * primitive and limit logic, on an mbarrier nothing is armed on, giving up
+ * after `rounds` rounds (1..1024), and synchronises the stream.  Returns
+ * PHYLO_ETIMEOUT when the wait expired and was reported (the expected
+ * result), PHYLO_OK if the flag stayed clear, PHYLO_EINVAL for a bad
+ * `rounds`, PHYLO_ECUDA on a CUDA error.  Nothing is left in flight, so the
+ * CUDA context stays usable.  Uses a static device word, not the heap. */
+int phylo_selftest_bounded_wait(int rounds, void* stream);
+
 /* Message for the last error on ctx (or for the last failed phylo_create
  * when ctx is NULL).  Valid until the next call on ctx. */
 const char* phylo_last_error(const phylo_ctx* ctx);
 
-/* No-allocation evaluation (the paper has no counterpart: it exists for
- * callers that cannot allocate device memory -- code that runs while a
- * stream capture is active in global mode, where cudaMalloc is illegal;
- * runtimes that own all device memory through their own pools; fixed-
- * footprint samplers that must not grow after start-up).
+/* No-allocation evaluation (the paper has no counterpart).  It exists for
+ * callers that cannot allocate device memory: runtimes that own all of the
+ * GPU's memory through their own pools and forbid side allocations, and
+ * fixed-footprint samplers or embedded services that must not grow their
+ * memory use after start-up.  cudaMalloc is either unavailable to them or
+ * would break their memory accounting.
  *
  * One FP32 evaluation of log P(Y) and its gradient, as phylo_evaluate,
  * from host inputs to host outputs, without a context or a workspace.  All
@@ -236,23 +257,24 @@ const char* phylo_last_error(const phylo_ctx* ctx);
  * process exits.  Limits: 2 <= n_tips <= 512, 2 <= n_states <= 64,
  * 1 <= n_categories <= 8, and the problem's buffers must fit in 32 MiB
  * (e.g. 64 tips x 4,000 patterns x 4 states x 4 categories); larger
- * problems return PHYLO_EINVAL with a message naming the bytes needed.
- * Arguments as in phylo_set_tree / phylo_set_tip_states /
- * phylo_set_pattern_weights / phylo_set_eigen / phylo_set_categories /
- * phylo_set_branch_lengths (all host pointers, validated first);
- * gradient may be NULL; error_message (may be NULL) receives up to
- * error_capacity bytes of text on failure.
+ * problems return PHYLO_EINVAL with a message naming the bytes needed,
+ * before any CUDA call.  Arguments as in phylo_set_tree /
+ * phylo_set_tip_states / phylo_set_pattern_weights / phylo_set_eigen /
+ * phylo_set_categories / phylo_set_branch_lengths (all host pointers,
+ * validated first); gradient may be NULL; error_message (may be NULL)
+ * receives up to error_capacity bytes of text on failure.
  *
- * The first call on a device looks the array's device address up
- * (cudaGetSymbolAddress) and sets kernel attributes for that device; make
- * that first call before any stream capture begins.  Calls allocate no
- * device or pinned memory.  Every call on a device shares the same array
- * and finds it holding the previous call's contents (the call clears the
- * one word it reads before writing).  Calls are synchronous (the stream is
- * synchronised before returning) and serialised within a process; device
- * work that overlaps a call while touching the same array -- e.g. a second
- * process cannot, but kernels launched by another thread of this process
- * from a copy of the array's address would -- races with it. */
+ * The first call on a device, with that device current, looks the array's
+ * device address up (cudaGetSymbolAddress) and sets kernel attributes for
+ * that device.  Calls allocate no device or pinned memory and call no
+ * allocating library routine.  Every call on a device shares the same
+ * array and finds it holding the previous call's contents (the call clears
+ * the one word it reads before writing).  Calls are synchronous: the stream
+ * is synchronised before returning, on error paths too once device work has
+ * been queued.  Calls are serialised within a process; device work that
+ * overlaps a call while touching the same array (kernels launched by
+ * another thread of this process from a copy of the array's address) races
+ * with it. */
 int phylo_evaluate_noalloc(int n_tips, int n_patterns, int n_states,
                            int n_categories, const int32_t* parent,
                            const uint8_t* tip_states,

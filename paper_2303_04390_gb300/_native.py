@@ -50,8 +50,9 @@ SIGNATURES = {
     "phylo_evaluate_device": (_c_int, [_vp, _vp]),
     "phylo_evaluate_device_timed": (_c_int, [_vp, _vp,
                                              ctypes.POINTER(_vp)]),
-    "phylo_forward_device": (_c_int, [_vp, _vp]),
-    "phylo_backward_device": (_c_int, [_vp, _vp]),
+    "phylo_forward_device": (_c_int, [_vp, _vp,
+                                      ctypes.POINTER(ctypes.c_uint64)]),
+    "phylo_backward_device": (_c_int, [_vp, _vp, ctypes.c_uint64]),
     "phylo_gradient_rate_time": (_c_int, [_vp, _vp, _vp, _vp, _vp, _c_int]),
     "phylo_gradient_heights": (_c_int, [_vp, _vp, _vp, _c_int]),
     "phylo_gradient_branch_sum": (_c_int, [_vp, _vp, _vp, _c_int, _vp, _c_int]),
@@ -59,6 +60,7 @@ SIGNATURES = {
     "phylo_launches_per_evaluation": (_c_int, [_vp]),
     "phylo_level_counts": (_c_int, [_vp, ctypes.POINTER(_c_int),
                                     ctypes.POINTER(_c_int)]),
+    "phylo_selftest_bounded_wait": (_c_int, [_c_int, _vp]),
     "phylo_last_error": (ctypes.c_char_p, [_vp]),
     "phylo_destroy": (_c_int, [_vp]),
     "phylo_evaluate_noalloc": (_c_int, [_c_int, _c_int, _c_int, _c_int, _ip,

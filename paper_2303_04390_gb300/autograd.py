@@ -8,7 +8,11 @@ backward(g):     the pre-order pass with the fused gradient kernel
                  rule for t = exp(log_t) multiplies by t.
 
 Both run on the context's stream; the log-likelihood and the gradient stay
-on the device.
+on the device.  Each forward carries the generation number the library
+gave its post-order pass; backward passes it back, and the library refuses
+(PHYLO_ESTATE) if another pass has rewritten the context's partials since,
+so two forwards on one context before a backward raise instead of
+returning the second forward's gradient for the first graph.
 """
 from __future__ import annotations
 
@@ -33,8 +37,11 @@ class BranchLogLik(torch.autograd.Function):
         t = torch.exp(log_t).contiguous()
         phylo_ctx.set_branch_lengths(t)
         out = torch.empty(1, dtype=torch.float64, device=log_t.device)
-        phylo_ctx._check(N.load().phylo_forward_device(phylo_ctx._ctx, _ptr(out)))
+        gen = ctypes.c_uint64(0)
+        phylo_ctx._check(N.load().phylo_forward_device(
+            phylo_ctx._ctx, _ptr(out), ctypes.byref(gen)))
         fctx.phylo_ctx = phylo_ctx
+        fctx.generation = gen.value
         fctx.save_for_backward(t)
         return out[0]
 
@@ -43,7 +50,8 @@ class BranchLogLik(torch.autograd.Function):
         (t,) = fctx.saved_tensors
         pc = fctx.phylo_ctx
         g = torch.empty_like(t)
-        pc._check(N.load().phylo_backward_device(pc._ctx, _ptr(g)))
+        pc._check(N.load().phylo_backward_device(pc._ctx, _ptr(g),
+                                                 fctx.generation))
         return grad_out * g * t, None
 
 

@@ -18,8 +18,11 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/phylo_api.h"
 #include "phylo_internal.h"
+#include "tma.cuh"
 
 using namespace phylo;
 
@@ -154,6 +157,7 @@ struct phylo_ctx {
   cudaGraphExec_t fwd_exec = nullptr;  // matrices + post-order + logL reduction
   cudaGraphExec_t bwd_exec = nullptr;  // pre-order + gradient reduction
   bool forward_valid = false;          // post-order partials match the inputs
+  uint64_t partials_gen = 0;           // bumped by every launch that rewrites them
   bool have_grad = false;              // out holds the gradient of an evaluation
   bool eig_reversible = false;         // V, Vinv are the symmetric decomposition
   bool graph_dirty = true;
@@ -194,6 +198,24 @@ int cuda_fail(phylo_ctx* ctx, cudaError_t e, const char* what) {
   return fail(ctx, PHYLO_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e),
               cudaGetErrorString(e));
 }
+
+// NVTX range with an integer payload (a level index); visible to profilers
+// for direct launches and for graph launches (the range spans the launch).
+struct NvtxRange {
+  NvtxRange(const char* name, int payload = -1) {
+    nvtxEventAttributes_t a{};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = name;
+    if (payload >= 0) {
+      a.payloadType = NVTX_PAYLOAD_TYPE_INT32;
+      a.payload.iValue = payload;
+    }
+    nvtxRangePushEx(&a);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define CUDA_TRY(ctx, call, what)                       \
   do {                                                  \
@@ -269,6 +291,7 @@ template <typename T>
 cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
   cudaError_t e = cudaSuccess;
   if (phase == 0) {
+    NvtxRange range("phylo matrices (Eq. 1)");
     e = cudaMemsetAsync(flag_word(ctx), 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     PmatArgs pa{};
@@ -294,6 +317,8 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     const int4* desc = ctx->dev<int4>(post ? ctx->L.post_desc : ctx->L.pre_desc);
     const std::vector<int>& off = post ? ctx->post_off : ctx->pre_off;
     for (size_t l = 0; l + 1 < off.size(); ++l) {
+      NvtxRange range(post ? "phylo post-order level (Eq. 2)"
+                           : "phylo pre-order level (Eqs. 4, 8)", (int)l);
       a.level_nodes = nodes + off[l];
       a.level_desc = desc + off[l];
       a.n_level = off[l + 1] - off[l];
@@ -306,6 +331,7 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     if (!post && ctx->C > 0) return launch_pre_finish<T>(a, ctx->L.SP, st);
     return cudaSuccess;
   }
+  NvtxRange range("phylo reduction (Eq. 7)");
   ReduceArgs ra{};
   ra.gpart = ctx->dev<double>(ctx->L.gpart);
   ra.lpart = ctx->dev<double>(ctx->L.lpart);
@@ -537,6 +563,8 @@ int check_ready(phylo_ctx* ctx) {
 int launch_eval(phylo_ctx* ctx) {
   int rc = check_ready(ctx);
   if (rc) return rc;
+  NvtxRange range("phylo evaluate");
+  ++ctx->partials_gen;
   if (ctx->flags & PHYLO_FLAG_NO_GRAPH) {
     rc = run_phases(ctx, 0, kPhases - 1, nullptr);
     if (rc) return rc;
@@ -635,6 +663,20 @@ int upload_typed(phylo_ctx* ctx, const Region& r, const double* host, size_t cou
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }
   return PHYLO_OK;
+}
+
+// Self-test of the bounded waits: one CTA waits on an mbarrier that expects
+// one arrival which never comes (nothing is armed on it: no copy, no MMA),
+// with the same primitive and the same timeout report (ERR_TIMEOUT in the
+// flag word) as the level kernels, then returns.
+__device__ int g_selftest_flag;
+
+__global__ void selftest_wait_kernel(int* flag, unsigned rounds) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
+  __syncthreads();
+  if (!__syncthreads_and(mbar_wait(&bar, 0, rounds)) && threadIdx.x == 0)
+    atomicOr(flag, ERR_TIMEOUT);
 }
 
 }  // namespace
@@ -1020,6 +1062,9 @@ int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out, void* const* events
     rc = build_phase_graphs(ctx);
     if (rc) return rc;
   }
+  ++ctx->partials_gen;
+  ctx->forward_valid = true;
+  ctx->have_grad = true;
   for (int ph = 0; ph < kPhases; ++ph) {
     CUDA_TRY(ctx, cudaEventRecord(static_cast<cudaEvent_t>(events[ph]), ctx->stream),
              "cudaEventRecord");
@@ -1035,11 +1080,14 @@ int phylo_evaluate_device_timed(phylo_ctx* ctx, double* out, void* const* events
   return PHYLO_OK;
 }
 
-int phylo_forward_device(phylo_ctx* ctx, double* out) {
+int phylo_forward_device(phylo_ctx* ctx, double* out, uint64_t* generation) {
   if (!ctx) return PHYLO_EINVAL;
   if (!out) return fail(ctx, PHYLO_EINVAL, "out is NULL");
   int rc = check_ready(ctx);
   if (rc) return rc;
+  NvtxRange range("phylo forward");
+  ++ctx->partials_gen;
+  ctx->forward_valid = false;
   // matrices and post-order levels, then the log-likelihood alone
   if (ctx->flags & PHYLO_FLAG_NO_GRAPH) {
     rc = run_phases(ctx, 0, 1, nullptr);
@@ -1055,6 +1103,7 @@ int phylo_forward_device(phylo_ctx* ctx, double* out) {
   }
   if (rc) return rc;
   ctx->forward_valid = true;
+  if (generation) *generation = ctx->partials_gen;
   if (out != ctx->dev<double>(ctx->L.out))
     CUDA_TRY(ctx, cudaMemcpyAsync(out, ctx->dev<double>(ctx->L.out), 8,
                                   cudaMemcpyDeviceToDevice, ctx->stream),
@@ -1062,11 +1111,17 @@ int phylo_forward_device(phylo_ctx* ctx, double* out) {
   return PHYLO_OK;
 }
 
-int phylo_backward_device(phylo_ctx* ctx, double* out) {
+int phylo_backward_device(phylo_ctx* ctx, double* out, uint64_t generation) {
   if (!ctx) return PHYLO_EINVAL;
   if (!out) return fail(ctx, PHYLO_EINVAL, "out is NULL");
   if (!ctx->forward_valid)
     return fail(ctx, PHYLO_ESTATE, "backward needs a forward pass on the current inputs");
+  if (generation != ctx->partials_gen)
+    return fail(ctx, PHYLO_ESTATE,
+                "backward of forward %llu, but the partials now belong to a later "
+                "pass (%llu): run that forward again",
+                (unsigned long long)generation, (unsigned long long)ctx->partials_gen);
+  NvtxRange range("phylo backward");
   int rc;
   if (ctx->flags & PHYLO_FLAG_NO_GRAPH) rc = run_phases(ctx, 2, 3, nullptr);
   else rc = run_phases(ctx, 2, 3, &ctx->bwd_exec);
@@ -1219,6 +1274,27 @@ int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
   *n_post_levels = ctx->have_tree ? (int)ctx->post_off.size() - 1 : 0;
   *n_pre_levels = ctx->have_tree ? (int)ctx->pre_off.size() - 1 : 0;
   return PHYLO_OK;
+}
+
+int phylo_selftest_bounded_wait(int rounds, void* stream) {
+  if (rounds < 1 || rounds > 1024)
+    return fail(nullptr, PHYLO_EINVAL, "rounds must be in [1, 1024]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* flag = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&flag), g_selftest_flag);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
+  if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaMemsetAsync");
+  selftest_wait_kernel<<<1, 32, 0, st>>>(flag, (unsigned)rounds);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(nullptr, e, "launch");
+  int flags = 0;
+  if ((e = cudaMemcpyAsync(&flags, flag, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "read flag");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaStreamSynchronize");
+  if (flags & ERR_TIMEOUT)
+    return fail(nullptr, PHYLO_ETIMEOUT, "device flagged: a bounded wait expired (self-test)");
+  return read_flags(nullptr, flags);
 }
 
 const char* phylo_last_error(const phylo_ctx* ctx) {

@@ -3,18 +3,18 @@
 // post- and pre-order partials, exponents, per-tile sums) placed in one
 // statically sized device array instead of a caller workspace.
 //
-// Who needs it: callers that must not allocate device memory at all -- code
-// running while another library holds a CUDA stream capture in global mode
-// (cudaMalloc is illegal there), runtimes whose memory is owned by their own
-// pool and forbid side allocations, and fixed-footprint embedded samplers
-// that must not grow their memory use after start-up.  They pass their
-// inputs and receive the results; nothing is allocated per call.
+// Who needs it: callers that must not allocate device memory at all --
+// runtimes whose GPU memory is owned by their own pool and that forbid side
+// allocations, and fixed-footprint samplers or embedded services that must
+// not grow their memory use after start-up.  They pass their inputs and
+// receive the results; nothing is allocated per call.
 //
 // The array below is part of the library image: every GPU that loads the
 // library keeps kNoAllocScratchBytes reserved until the process exits.
 // Host code may only use its name to look its device address up with
 // cudaGetSymbolAddress (done once per device, on the first call on that
-// device); the name itself is a host-side stand-in, not a device address.
+// device, with that device current); the name itself is a host-side
+// stand-in, not a device address, so it is never passed to a kernel.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -271,6 +271,14 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   if (rc) return rc;
   char* ws = static_cast<char*>(base);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Declared after the lock, so it runs before the lock is released: once
+  // work is queued on the stream, every return path (the error returns of
+  // NA_TRY included) waits for that work, so no queued copy or kernel still
+  // touches the shared array when the next call takes the lock.
+  struct DrainOnExit {
+    cudaStream_t st;
+    ~DrainOnExit() { (void)cudaStreamSynchronize(st); }
+  } drain{st};
   auto up = [&](const NaRegion& r, const void* src, size_t bytes) {
     return bytes ? cudaMemcpyAsync(ws + r.off, src, bytes, cudaMemcpyHostToDevice, st)
                  : cudaSuccess;

@@ -57,8 +57,38 @@ def test_backward_needs_forward():
     g = torch.empty(2 * w.n_tips - 2, dtype=torch.float64, device="cuda")
     import ctypes
     from paper_2303_04390_gb300 import _native as N
-    rc = N.load().phylo_backward_device(ctx._ctx, ctypes.c_void_p(g.data_ptr()))
+    rc = N.load().phylo_backward_device(ctx._ctx, ctypes.c_void_p(g.data_ptr()), 0)
     assert rc == N.PHYLO_ESTATE
+
+
+def test_two_forwards_then_backward_is_refused():
+    """Two forwards on one context before a backward: the first graph's
+    backward is refused (its partials were overwritten), the second's is
+    right, and re-running the first forward makes its backward right."""
+    import paper_2303_04390_gb300 as pg
+    w = synth.small_workload(16, 4, 4, 90, seed=35)
+    ctx = pg.from_workload(w, "fp32")
+    lt1 = torch.tensor(np.log(w.t), dtype=torch.float64, device="cuda",
+                       requires_grad=True)
+    lt2 = torch.tensor(np.log(w.t * 1.3), dtype=torch.float64, device="cuda",
+                       requires_grad=True)
+    ll1 = pg.branch_loglik(lt1, ctx)
+    ll2 = pg.branch_loglik(lt2, ctx)
+    with pytest.raises(pg.PhyloError) as e:
+        ll1.backward()
+    assert e.value.code == -4  # PHYLO_ESTATE
+    ll2.backward()
+    ref2 = oracle_eval(w, t=w.t * 1.3)
+    tol = TOL["fp32"]
+    want = ref2[1] * w.t * 1.3
+    bound = np.maximum(tol["g_rel"] * np.abs(want), tol["g_cond"] * ref2[3] * w.t * 1.3)
+    assert np.all(np.abs(lt2.grad.cpu().numpy() - want) <= bound)
+    lt1b = lt1.detach().clone().requires_grad_(True)
+    pg.branch_loglik(lt1b, ctx).backward()
+    ref1 = oracle_eval(w)
+    want = ref1[1] * w.t
+    bound = np.maximum(tol["g_rel"] * np.abs(want), tol["g_cond"] * ref1[3] * w.t)
+    assert np.all(np.abs(lt1b.grad.cpu().numpy() - want) <= bound)
 
 
 def test_forward_backward_agree_with_evaluate_over_steps():

@@ -1,9 +1,11 @@
-"""The no-allocation entry point (phylo_evaluate_noalloc): for callers that
-cannot allocate device memory, e.g. while a global-mode stream capture is
-active or inside a runtime that owns all device memory.  Its result must
-agree with the workspace path (phylo_evaluate) within the FP32 tolerances
-of the parity tests, on two calls in a row (the second finds the static
-scratch holding the first call's contents).  Collected last on purpose."""
+"""The no-allocation entry point (phylo_evaluate_noalloc), for callers that
+cannot allocate device memory: runtimes whose GPU memory belongs to their
+own pool, and fixed-footprint samplers that must not grow after start-up.
+Its result must agree with the workspace path (phylo_evaluate) within the
+FP32 tolerances of the parity tests, on two calls in a row (the second
+finds the static scratch holding the first call's contents).  Collected
+last on purpose, so that a failure here stops a -x run only after every
+other test has run."""
 import ctypes
 
 import numpy as np
