@@ -12,14 +12,21 @@ Printed as one JSON line:
   e2e        evals/s through the C ABI with host buffers: each step copies
              the branch lengths from pinned host memory and reads log P(Y)
              and the gradient back
+  ms_per_step_stats  p10 / p50 / p90 of the per-step device times (a CUDA
+             event between consecutive steps)
   roofline   the dominant kernel (the phase with the largest device time)
              against the measured HBM copy bandwidth
   fp64_path  the plain FP64 path on the same workload and GPU
-  cpu_baseline the FP64 oracle on the host (bounded pattern sample)
+  extra      every other workload (codon-128, aa-256, mmm-122, jc69-8): the
+             same device measurements, phases, rooflines and FP64 path
+  cpu_baseline the FP64 oracle on the host: full evaluations on all host
+             cores (one worker per core over pattern blocks) and on one
+             thread
   served     the continuous-batching request loop on a Poisson stream of
              independent requests (p50/p99 latency, evals/s)
 
---impl reference times the oracle as the reference arm.
+--impl reference times the oracle (all host cores, full evaluations) as
+the reference arm.
 Under torchrun each rank runs an independent replica (weak scaling, no
 collective on the data path; a MAX all-reduce of the elapsed time only).
 """
@@ -158,86 +165,154 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# Oracle timing (the CPU baseline and the reference arm)
+# Oracle timing (the CPU baseline and the reference arm).  The oracle runs as
+# it stands: one evaluation per contiguous pattern block, each block in its
+# own spawned worker process with one BLAS/OpenMP thread (the paper's CPU
+# scheme: threads over pattern blocks); log P(Y) and the gradient are sums
+# over patterns, so the blocks' results are summed.
 # ---------------------------------------------------------------------------
 
-def _oracle_sample_run(name, seed, n_patterns):
-    """Runs in a spawned process with one BLAS/OpenMP thread."""
-    import synth  # noqa: F401
+_POOL_W = None
+
+
+def _pool_init(name, seed, n_tips, n_patterns):
+    global _POOL_W
+    kw = {}
+    if n_tips:
+        kw["n_tips"] = n_tips
+    if n_patterns:
+        kw["n_patterns"] = n_patterns
+    _POOL_W = _workloads()[name][0](seed, **kw)
+
+
+def _pool_eval(lo, hi):
     from oracle import phylo_oracle as O
-    w = _workloads()[name][0](seed)
-    ws = w.with_patterns(0, n_patterns)
-    t0 = time.perf_counter()
-    O.evaluate(ws.parent, ws.t, ws.Q, ws.pi, ws.rates, ws.weights,
-               ws.pattern_weights, tip_states=ws.tip_states)
-    return time.perf_counter() - t0, w.n_patterns
+    ws = _POOL_W.with_patterns(lo, hi)
+    ll, g, _ = O.evaluate(ws.parent, ws.t, ws.Q, ws.pi, ws.rates, ws.weights,
+                          ws.pattern_weights, tip_states=ws.tip_states)
+    return ll, g
 
 
-def _oracle_pool():
-    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
-    old = {k: os.environ.get(k) for k in env_keys}
-    for k in env_keys:
-        os.environ[k] = "1"
+class OraclePool:
+    """n_workers spawned processes, each holding the workload; evaluate()
+    runs one full evaluation (or the first n_patterns patterns) split into
+    n_workers contiguous pattern blocks and returns its wall time."""
+
+    def __init__(self, name, n_workers, seed=0, n_tips=None, n_patterns=None):
+        env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        old = {k: os.environ.get(k) for k in env_keys}
+        for k in env_keys:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(
+                n_workers, initializer=_pool_init,
+                initargs=(name, seed, n_tips, n_patterns))
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.n = n_workers
+
+    def evaluate(self, n_patterns):
+        bounds = [round(n_patterns * i / self.n) for i in range(self.n + 1)]
+        jobs = [(a, b) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+        t0 = time.perf_counter()
+        parts = self.pool.starmap(_pool_eval, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+        return dt, sum(p[0] for p in parts)
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def host_cores():
     try:
-        return mp.get_context("spawn").Pool(1)
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(name, n_patterns, n_tips=None, repeats=3):
+    """The oracle on full evaluations of the workload: on all host cores
+    (median of `repeats` after one warm-up) and on one thread (one
+    evaluation)."""
+    cores = host_cores()
+    multi = OraclePool(name, cores, n_tips=n_tips, n_patterns=None)
+    try:
+        multi.evaluate(n_patterns)  # warm-up (imports, first-touch)
+        t_multi = statistics.median(multi.evaluate(n_patterns)[0]
+                                    for _ in range(repeats))
     finally:
-        for k, v in old.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-
-
-def cpu_baseline(name, seed=0, target_s=15.0):
-    """Oracle evaluations/s of the full workload from a bounded pattern
-    sample.  The oracle's cost is a fixed part (transition matrices) plus a
-    part linear in the pattern count, so two sample sizes are timed and the
-    full-workload time is extrapolated linearly from them."""
-    with _oracle_pool() as pool:
-        n_a = 100
-        t_a, C = pool.apply(_oracle_sample_run, (name, seed, n_a))
-        n_b = int(min(C, max(4 * n_a, n_a * target_s / max(t_a, 1e-3))))
-        t_b, C = pool.apply(_oracle_sample_run, (name, seed, n_b))
-    slope = max(t_b - t_a, 1e-9) / max(n_b - n_a, 1)
-    t_full = t_b + slope * (C - n_b)
-    return {"value": 1.0 / t_full, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle (numpy, 1 thread) timed on the first "
-                      f"{n_a} and {n_b} of {C} patterns ({t_a:.2f} s, "
-                      f"{t_b:.2f} s), full-workload time {t_full:.1f} s "
-                      f"extrapolated linearly in the pattern count"}
+        multi.close()
+    single = OraclePool(name, 1, n_tips=n_tips)
+    try:
+        t_single = single.evaluate(n_patterns)[0]
+    finally:
+        single.close()
+    return {"value": 1.0 / t_multi, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"full evaluations ({n_patterns} patterns) of the FP64 "
+                      f"oracle (numpy), {cores} spawned workers with one "
+                      f"thread each over contiguous pattern blocks: median "
+                      f"of {repeats} after one warm-up, {t_multi:.2f} s each",
+            "single_thread": {"value": 1.0 / t_single, "unit": UNIT,
+                              "cores": 1,
+                              "sample": f"one full evaluation on one thread, "
+                                        f"{t_single:.1f} s"}}
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, on every host core (one
+    worker per core over contiguous pattern blocks), each step one full
+    evaluation of the workload -- or, where W + K full evaluations would
+    not end within about four minutes, the first n patterns of it, n sized
+    to fit and stated."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     name = args.workload
-    budget = 150.0
-    with _oracle_pool() as pool:
-        t_cal, C = pool.apply(_oracle_sample_run, (name, 0, 100))
-        per_step = budget / (args.steps + args.warmup)
-        n = int(min(C, max(10, 100 * per_step / max(t_cal, 1e-3))))
-        for _ in range(args.warmup):
-            pool.apply(_oracle_sample_run, (name, 0, n))
-        times = []
-        for _ in range(args.steps):
-            t, _ = pool.apply(_oracle_sample_run, (name, 0, n))
-            times.append(t)
+    precision = _workloads()[name][1]
+    kw = {}
+    if args.taxa:
+        kw["n_tips"] = args.taxa
+    if args.patterns:
+        kw["n_patterns"] = args.patterns
+    C = _workloads()[name][0](0, **kw).n_patterns
+    cores = host_cores()
+    pool = OraclePool(name, cores, n_tips=args.taxa, n_patterns=args.patterns)
+    try:
+        t_cal, _ = pool.evaluate(C)  # also the first warm-up step
+        budget = 240.0
+        n = C
+        if t_cal * (args.steps + args.warmup) > budget:
+            n = max(cores, int(C * budget / (t_cal * (args.steps + args.warmup))))
+        for _ in range(args.warmup - 1):
+            pool.evaluate(n)
+        times = [pool.evaluate(n)[0] for _ in range(args.steps)]
+    finally:
+        pool.close()
     total = sum(times)
     value = args.steps * (n / C) / total
-    precision = _workloads()[name][1]
+    what = (f"each step one full evaluation ({C} patterns)" if n == C else
+            f"each step one evaluation of the first {n} of {C} patterns "
+            f"(a full evaluation takes {t_cal:.1f} s), rate scaled by {n}/{C}")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / args.steps * (C / n),
+        "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": name, "precision_of_our_arm": precision},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
                          "kind": "oracle",
-                         "sample": f"each step: one FP64 oracle evaluation "
-                                   f"on the first {n} of {C} patterns, "
-                                   f"scaled by {C}/{n}"},
+                         "sample": f"{what}; FP64 oracle (numpy), {cores} "
+                                   f"spawned workers with one thread each "
+                                   f"over contiguous pattern blocks; step "
+                                   f"times median {statistics.median(times):.2f}"
+                                   f" s"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -324,6 +399,177 @@ def run_served(args, seed=0):
     }
 
 
+def _percentiles(ms_list):
+    a = sorted(ms_list)
+
+    def q(f):
+        if not a:
+            return None
+        x = f * (len(a) - 1)
+        lo = int(math.floor(x))
+        hi = min(lo + 1, len(a) - 1)
+        return a[lo] + (a[hi] - a[lo]) * (x - lo)
+    return {"p10": q(0.1), "p50": q(0.5), "p90": q(0.9)}
+
+
+class Measure:
+    """Times one workload on the device: K steps after W warm-up steps, each
+    step new branch lengths (already on the device) and one evaluation,
+    with a CUDA event between consecutive steps on the launching stream;
+    then the four phases over up to 200 more evaluations."""
+
+    def __init__(self, pg, w, precision, stream, seed):
+        import numpy as np
+        import torch
+        self.torch = torch
+        self.w, self.precision, self.stream = w, precision, stream
+        self.ctx = pg.from_workload(w, precision, stream=stream)
+        self.nb = 2 * w.n_tips - 2
+        self.rng = np.random.default_rng(seed)
+        self.out = torch.empty(2 * w.n_tips - 1, dtype=torch.float64,
+                               device="cuda")
+
+    def branch_lengths(self, n):
+        import numpy as np
+        t = self.w.t[None, :] * np.exp(
+            0.05 * self.rng.standard_normal((n, self.nb)))
+        return t, self.torch.tensor(t, dtype=self.torch.float64, device="cuda")
+
+    def steps(self, K, W, barrier):
+        torch = self.torch
+        _, t_dev = self.branch_lengths(K + W)
+        for i in range(W):
+            self.ctx.set_branch_lengths(t_dev[i])
+            self.ctx.evaluate_device(self.out)
+        self.ctx.check()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        barrier()
+        evs[0].record(self.stream)
+        for i in range(K):
+            self.ctx.set_branch_lengths(t_dev[W + i])
+            self.ctx.evaluate_device(self.out)
+            evs[i + 1].record(self.stream)
+        barrier()
+        self.ctx.check()
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+        return evs[0].elapsed_time(evs[K]), per
+
+    def phases(self, n_ev, barrier):
+        torch = self.torch
+        _, t_dev = self.branch_lengths(n_ev)
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]
+               for _ in range(n_ev)]
+        barrier()
+        for i in range(n_ev):
+            self.ctx.set_branch_lengths(t_dev[i])
+            self.ctx.evaluate_device_timed(evs[i], self.out)
+        barrier()
+        self.ctx.check()
+        ms = [0.0] * 4
+        for e in evs:
+            for p in range(4):
+                ms[p] += e[p].elapsed_time(e[p + 1])
+        return [x / n_ev for x in ms]
+
+    def close(self):
+        self.ctx.close()
+
+
+def fp64_path(pg, w, stream, K, barrier):
+    """The plain FP64 path on the same workload: K timed steps."""
+    m = Measure(pg, w, "fp64", stream, seed=77)
+    try:
+        ms, per = m.steps(K, 3, barrier)
+    finally:
+        m.close()
+    by64 = algorithmic_bytes(w, "fp64")
+    return {"value": K / (ms / 1e3), "unit": UNIT, "steps": K,
+            "ms_per_step": _percentiles(per),
+            "hbm_gbs_all_phases": sum(by64.values()) / (ms / K / 1e3) / 1e9}
+
+
+def rooflines(w, precision, phase_ms, level_counts, peaks, n_sm, workload):
+    """The dominant phase against its bound: HBM for 4 and 20 states (with
+    the FP32 ALU rate beside it at 20 states), the tensor pipe for the
+    tensor-core path (21-64 states, FP32; the HBM figure is the main
+    roofline there too), the FP32 (FP64) ALU rate for 65-256 states."""
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_kind = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+    by = algorithmic_bytes(w, precision)
+    fl = algorithmic_flops(w)
+    names = ["pmat", "post", "pre", "reduce"]
+    kernels = {"pmat": "pmat_kernel", "post": "post-order level kernel",
+               "pre": "pre-order level kernel (fused gradient)",
+               "reduce": "reduce_kernel"}
+    if precision == "fp32" and 20 < w.n_states <= 64:
+        kernels = {"pmat": "pmat_tc_kernel", "post": "post_tc_pipe_kernel",
+                   "pre": "pre_tc_kernel + ratio_tc_kernel",
+                   "reduce": "reduce_kernel"}
+    phases = {}
+    for n_, ms_ in zip(names, phase_ms):
+        phases[n_] = {"ms": ms_, "algorithmic_bytes": by[n_],
+                      "achieved_gbs": by[n_] / (ms_ / 1e3) / 1e9 if ms_ > 0 else None}
+    dom = max(names, key=lambda n_: phases[n_]["ms"])
+    n_launch_dom = {"pmat": 1, "reduce": 1}.get(dom)
+    if n_launch_dom is None:
+        n_launch_dom = level_counts[0 if dom == "post" else 1]
+    achieved = phases[dom]["achieved_gbs"]
+    tr = _traffic_record(dom, workload, precision)
+    traffic = tr[0] if tr is not None else None
+    mhz = peaks.get("sm_max_mhz") or 2070.0
+    alu_peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+    alu_kind = f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
+    roofline = {
+        "bound": "hbm", "kernel": kernels[dom], "achieved": achieved,
+        "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+        "peak_kind": f"{peak_kind} (HBM copy, burst)",
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": by[dom] / n_launch_dom,
+        "launches_per_evaluation": n_launch_dom,
+        "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
+    }
+    if 4 < w.n_states <= 20 and precision == "fp32":
+        aach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
+        roofline["alu"] = {"achieved": aach, "peak": alu_peak, "unit": "TFLOP/s",
+                           "frac": aach / alu_peak, "peak_kind": alu_kind,
+                           "algorithmic_flops_per_launch": fl[dom] / n_launch_dom}
+    if w.n_states > 64:
+        if precision == "fp32":
+            apeak, akind = alu_peak, alu_kind
+        else:
+            apeak, akind = 1.25, "nominal FP64 rate"
+        aach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
+        roofline = {
+            "bound": "alu", "kernel": kernels[dom], "achieved": aach, "peak": apeak,
+            "unit": "TFLOP/s", "frac": aach / apeak, "peak_kind": akind,
+            "traffic": traffic,
+            "algorithmic_flops_per_launch": fl[dom] / n_launch_dom,
+            "launches_per_evaluation": n_launch_dom,
+            "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
+            "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak,
+                    "algorithmic_bytes_per_launch": by[dom] / n_launch_dom},
+        }
+    tensor = None
+    if precision == "fp32" and 20 < w.n_states <= 64:
+        tpeak = peaks.get("bf16_tflops_sustained")
+        tkind = "measured" if tpeak else "fallback"
+        tpeak = tpeak or 1700.0
+        tach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
+        rec = _profile_record(dom, workload, precision) or {}
+        tensor = {
+            "bound": "tensor", "kernel": kernels[dom], "achieved": tach,
+            "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
+            "peak_kind": f"{tkind} (BF16 dense, sustained)",
+            "algorithmic_flops_per_launch": fl[dom] / n_launch_dom,
+            "tensor_pipe_active_pct_ncu": (float(rec["tensor_pipe_active_pct"])
+                                           if "tensor_pipe_active_pct" in rec
+                                           else None),
+        }
+    return roofline, tensor, phases, sum(by.values())
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -351,226 +597,116 @@ def run_ours(args):
         kw["n_patterns"] = args.patterns
     w = make(rank, **kw)  # independent replica per rank
     stream = torch.cuda.current_stream()
-    ctx = pg.from_workload(w, precision, stream=stream)
     K, W = args.steps, args.warmup
     nb = 2 * w.n_tips - 2
-    # branch lengths of every step: log-normal jitter around the drawn ones
-    rng = np.random.default_rng(1000 + rank)
-    t_all = w.t[None, :] * np.exp(0.05 * rng.standard_normal((K + W, nb)))
-    t_dev = torch.tensor(t_all, dtype=torch.float64, device="cuda")
-    out = torch.empty(2 * w.n_tips - 1, dtype=torch.float64, device="cuda")
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    def step(i):
-        ctx.set_branch_lengths(t_dev[i])
-        ctx.evaluate_device(out)
+    def max_over_ranks(x):
+        if world > 1:
+            tt = torch.tensor([x], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            x = float(tt.item())
+        return x
 
-    sampler = ClockSampler(local)
-    for i in range(W):
-        step(i)
-    ctx.check()
+    m = Measure(pg, w, precision, stream, seed=1000 + rank)
     if args.profile:
-        # profiler target: the warm-up above, then K evaluations, nothing else
-        for i in range(K):
-            step(W + i)
-        ctx.check()
-        torch.cuda.synchronize()
+        # profiler target: W warm-up and K evaluations, nothing else
+        m.steps(K, W, barrier)
+        m.close()
         return
+    sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.2)
     # -- headline: device-resident inputs, one graph per evaluation --------
-    barrier()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for i in range(K):
-        step(W + i)
-    ev1.record(stream)
-    barrier()
-    ms = ev0.elapsed_time(ev1)
-    ctx.check()
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, per_step = m.steps(K, W, barrier)
+    ms = max_over_ranks(ms)
     value = world * K / (ms / 1e3)
-    launches = ctx.launches_per_evaluation()
-
+    launches = m.ctx.launches_per_evaluation()
+    level_counts = m.ctx.level_counts()
     # -- per-phase device times (four graph launches, events between) -----
-    n_ev = min(K, 200)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)]
-           for _ in range(n_ev)]
-    barrier()
-    for i in range(n_ev):
-        ctx.set_branch_lengths(t_dev[W + i])
-        ctx.evaluate_device_timed(evs[i], out)
-    barrier()
-    phase_ms = [0.0] * 4
-    for e in evs:
-        for p in range(4):
-            phase_ms[p] += e[p].elapsed_time(e[p + 1])
-    phase_ms = [x / n_ev for x in phase_ms]
-    ctx.check()
-
+    phase_ms = m.phases(min(max(K, 20), 200), barrier)
     # -- end to end through the C ABI with host buffers -------------------
+    t_all, _ = m.branch_lengths(K + 3)
     t_host = torch.tensor(t_all, dtype=torch.float64).pin_memory()
     ll_host = torch.empty(1, dtype=torch.float64).pin_memory()
     g_host = torch.empty(nb, dtype=torch.float64).pin_memory()
-    n_e2e = min(K, 500)
+    for i in range(3):
+        m.ctx.set_branch_lengths(t_host[i])
+        m.ctx.evaluate_into(ll_host, g_host)
+    n_e2e = K
     barrier()
     t0 = time.perf_counter()
     for i in range(n_e2e):
-        ctx.set_branch_lengths(t_host[W + i])
-        ctx.evaluate_into(ll_host, g_host)
+        m.ctx.set_branch_lengths(t_host[3 + i])
+        m.ctx.evaluate_into(ll_host, g_host)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = world * n_e2e / e2e_s
     sampler.stop()
     clocks = sampler.summary()
+    m.close()
 
-    # -- the plain FP64 path on the same workload -------------------------
-    fp64 = None
-    if precision != "fp64" and not args.skip_fp64:
-        ctx64 = pg.from_workload(w, "fp64", stream=stream)
-        n64 = max(5, min(K // 10, 100))
-        for i in range(3):
-            ctx64.set_branch_lengths(t_dev[i])
-            ctx64.evaluate_device(out)
-        barrier()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for i in range(n64):
-            ctx64.set_branch_lengths(t_dev[W + i])
-            ctx64.evaluate_device(out)
-        a1.record(stream)
-        barrier()
-        ms64 = a0.elapsed_time(a1)
-        ctx64.check()
-        by64 = algorithmic_bytes(w, "fp64")
-        fp64 = {"value": n64 / (ms64 / 1e3), "unit": UNIT, "steps": n64,
-                "hbm_gbs_all_phases": sum(by64.values()) / (ms64 / n64 / 1e3) / 1e9}
-        ctx64.close()
-
-    if rank != 0:
-        return
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    hbm_peak = peaks.get("hbm_gbs")
-    peak_kind = "measured" if hbm_peak else "fallback"
-    hbm_peak = hbm_peak or 6800.0
-    by = algorithmic_bytes(w, precision)
-    names = ["pmat", "post", "pre", "reduce"]
-    kernels = {"pmat": "pmat_kernel", "post": "post-order level kernel",
-               "pre": "pre-order level kernel (fused gradient)",
-               "reduce": "reduce_kernel"}
-    if precision == "fp32" and 20 < w.n_states <= 64:
-        kernels = {"pmat": "pmat_tc_kernel", "post": "post_tc_pipe_kernel",
-                   "pre": "pre_tc_kernel + ratio_tc_kernel",
-                   "reduce": "reduce_kernel"}
-    phases = {}
-    for n_, ms_ in zip(names, phase_ms):
-        phases[n_] = {"ms": ms_, "algorithmic_bytes": by[n_],
-                      "achieved_gbs": by[n_] / (ms_ / 1e3) / 1e9 if ms_ > 0 else None}
-    dom = max(names, key=lambda n_: phases[n_]["ms"])
-    n_launch_dom = {"pmat": 1, "reduce": 1}.get(dom)
-    if n_launch_dom is None:
-        n_launch_dom = ctx.level_counts()[0 if dom == "post" else 1]
-    achieved = phases[dom]["achieved_gbs"]
-    tr = _traffic_record(dom, args.workload, precision)
-    traffic = None
-    if tr is not None:
-        traffic = tr[0]
-    roofline = {
-        "bound": "hbm", "kernel": kernels[dom], "achieved": achieved,
-        "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-        "peak_kind": f"{peak_kind} (HBM copy)",
-        "traffic": traffic,
-        "algorithmic_bytes_per_launch": by[dom] / n_launch_dom,
-        "launches_per_evaluation": n_launch_dom,
-        "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
-    }
-    if 4 < w.n_states <= 20 and precision == "fp32":
-        # 20 states sit near the FP32 ridge (about 10 flop per byte moved):
-        # the CUDA-core rate of the same phase beside the HBM figure
-        fl = algorithmic_flops(w)
-        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = peaks.get("sm_max_mhz") or 2070.0
-        apeak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
-        aach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
-        roofline["alu"] = {"achieved": aach, "peak": apeak, "unit": "TFLOP/s",
-                           "frac": aach / apeak,
-                           "peak_kind": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x "
-                                        f"{mhz:.0f} MHz",
-                           "algorithmic_flops_per_launch": fl[dom] / n_launch_dom}
-    if w.n_states > 64:
-        # 65..256 states: the level kernels are CUDA-core contractions
-        # (about 2 S flop per byte moved), so the bound is the FP32 (FP64)
-        # arithmetic rate: SMs x 128 FP32 lanes x 2 flop x the maximum SM
-        # clock; FP64 takes the GB300's nominal 1.25 TFLOP/s
-        fl = algorithmic_flops(w)
-        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = peaks.get("sm_max_mhz") or 2070.0
-        if precision == "fp32":
-            apeak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
-            akind = f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
-        else:
-            apeak, akind = 1.25, "nominal FP64 rate"
-        aach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
-        roofline = {
-            "bound": "alu", "kernel": kernels[dom], "achieved": aach, "peak": apeak,
-            "unit": "TFLOP/s", "frac": aach / apeak, "peak_kind": akind,
-            "traffic": traffic,
-            "algorithmic_flops_per_launch": fl[dom] / n_launch_dom,
-            "launches_per_evaluation": n_launch_dom,
-            "avg_launch_ms": phases[dom]["ms"] / n_launch_dom,
-            "hbm": {"achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak,
-                    "algorithmic_bytes_per_launch": by[dom] / n_launch_dom},
-        }
-    tensor = None
-    if precision == "fp32" and 20 < w.n_states <= 64:
-        # the tensor-core path: algorithmic FLOP rate of its dominant phase
-        # against the sustained BF16 peak (its contractions run on BF16
-        # terms), and the tensor-pipe share ncu measured for that kernel
-        fl = algorithmic_flops(w)
-        tpeak = peaks.get("bf16_tflops_sustained")
-        tkind = "measured" if tpeak else "fallback"
-        tpeak = tpeak or 1700.0
-        tach = fl[dom] / (phases[dom]["ms"] / 1e3) / 1e12
-        rec = _profile_record(dom, args.workload, precision) or {}
-        tensor = {
-            "bound": "tensor", "kernel": kernels[dom], "achieved": tach,
-            "peak": tpeak, "unit": "TFLOP/s", "frac": tach / tpeak,
-            "peak_kind": f"{tkind} (BF16 dense, sustained)",
-            "algorithmic_flops_per_launch": fl[dom] / n_launch_dom,
-            "tensor_pipe_active_pct_ncu": (float(rec["tensor_pipe_active_pct"])
-                                           if "tensor_pipe_active_pct" in rec
-                                           else None),
-        }
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline, tensor, phases, bytes_all = rooflines(
+        w, precision, phase_ms, level_counts, peaks, n_sm, args.workload)
+
+    # -- the plain FP64 path on the same workload (>= 20 steps) -----------
+    fp64 = None
+    if precision != "fp64" and not args.skip_fp64:
+        fp64 = fp64_path(pg, w, stream, max(20, min(K, 100)), barrier)
+
+    # -- every other workload: the same measurements, in 'extra' ----------
+    extra = {}
+    if not args.skip_extras and not (args.taxa or args.patterns):
+        for name, (mk, prec) in _workloads().items():
+            if name == args.workload:
+                continue
+            wx = mk(rank)
+            mx = Measure(pg, wx, prec, stream, seed=2000 + rank)
+            try:
+                msx, perx = mx.steps(max(K, 20), max(W, 3), barrier)
+                kx = max(K, 20)
+                phx = mx.phases(min(max(K, 20), 200), barrier)
+                lcx = mx.ctx.level_counts()
+            finally:
+                mx.close()
+            rx, tx, phsx, _ = rooflines(wx, prec, phx, lcx, peaks, n_sm, name)
+            ent = {"value": world * kx / (max_over_ranks(msx) / 1e3),
+                   "unit": UNIT, "steps": kx, "precision": prec,
+                   "taxa": wx.n_tips, "patterns": wx.n_patterns,
+                   "states": wx.n_states, "categories": wx.n_categories,
+                   "ms_per_step": _percentiles(perx),
+                   "us_per_eval": msx / kx * 1e3,
+                   "phases_ms": {k_: v_["ms"] for k_, v_ in phsx.items()},
+                   "roofline": rx, "tensor_roofline": tx}
+            if prec != "fp64" and not args.skip_fp64:
+                ent["fp64_path"] = fp64_path(pg, wx, stream, 20, barrier)
+            extra[name] = ent
+
+    if rank != 0:
+        return
     served = None
     if not args.skip_serve:
         served = run_served(args)
     cpu = None
     if world == 1 and not args.skip_cpu:
-        cpu = cpu_baseline(args.workload)
+        cpu = cpu_baseline(args.workload, w.n_patterns, n_tips=args.taxa)
     s_pad = 4 if w.n_states <= 4 else 20 if w.n_states <= 20 else 64
     part_bytes = 2 * (w.n_tips - 1) * w.n_patterns * w.n_categories * \
         s_pad * (8 if precision == "fp64" else 4)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": ms / K,
+        "ms_per_step_stats": _percentiles(per_step),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if precision == "fp64" else "f32",
         "data": "synthetic",
@@ -591,14 +727,14 @@ def run_ours(args):
         "roofline": roofline,
         "tensor_roofline": tensor,
         "phases": phases,
-        "hbm_gbs_all_phases": sum(by.values()) / (ms / K / 1e3) / 1e9,
+        "hbm_gbs_all_phases": bytes_all / (ms / K / 1e3) / 1e9,
         "fp64_path": fp64,
+        "extra": extra,
         "served": served,
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
 
 
 def main():
@@ -617,6 +753,8 @@ def main():
     ap.add_argument("--patterns", type=int, default=None,
                     help="override the workload's number of patterns")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="time the chosen workload only (no 'extra' entries)")
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=96)
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)

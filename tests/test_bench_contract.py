@@ -55,3 +55,31 @@ def test_work_counts():
     fl = bench.algorithmic_flops(w)
     assert fl["post"] == (N - 2) * 2 * S * S * R * C
     assert fl["pre"] == 3 * fl["post"] and fl["pmat"] == 0
+
+
+def test_percentiles():
+    sys.path.insert(0, ROOT)
+    import bench
+    q = bench._percentiles([float(x) for x in range(11)])
+    assert q == {"p10": 1.0, "p50": 5.0, "p90": 9.0}
+
+
+def test_oracle_pool_blocks_sum_to_the_full_evaluation():
+    """The CPU baseline's pattern-block split: the blocks' log-likelihoods
+    sum to the oracle's full-workload value, and the baseline reports the
+    cores it used."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import phylo_oracle as O
+    w = synth.workload_jc69_8(0)
+    ll, _, _ = O.evaluate(w.parent, w.t, w.Q, w.pi, w.rates, w.weights,
+                          w.pattern_weights, tip_states=w.tip_states)
+    pool = bench.OraclePool("jc69-8", 3)
+    try:
+        dt, ll_blocks = pool.evaluate(w.n_patterns)
+    finally:
+        pool.close()
+    assert dt > 0 and abs(ll_blocks - ll) <= 1e-10 * abs(ll)
+    cpu = bench.cpu_baseline("jc69-8", w.n_patterns, repeats=1)
+    assert cpu["cores"] == bench.host_cores() and cpu["value"] > 0
+    assert cpu["single_thread"]["cores"] == 1
