@@ -221,8 +221,9 @@ int phylo_check(phylo_ctx* ctx);
 int phylo_launches_per_evaluation(const phylo_ctx* ctx);
 
 /* Length of the level schedule: the number of post-order launches (tree
- * height) and of pre-order launches (distinct depths of internal nodes).
- * Both 0 before the tree is set. */
+ * height, less the heights left empty by fused cherries on the FP32
+ * 4-state path) and of pre-order launches (distinct depths of internal
+ * nodes).  Both 0 before the tree is set. */
 int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
                        int* n_pre_levels);
 

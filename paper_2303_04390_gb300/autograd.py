@@ -10,9 +10,12 @@ backward(g):     the pre-order pass with the fused gradient kernel
 Both run on the context's stream; the log-likelihood and the gradient stay
 on the device.  Each forward carries the generation number the library
 gave its post-order pass; backward passes it back, and the library refuses
-(PHYLO_ESTATE) if another pass has rewritten the context's partials since,
-so two forwards on one context before a backward raise instead of
-returning the second forward's gradient for the first graph.
+(PHYLO_ESTATE) if another pass has rewritten the context's partials since.
+Backward then runs this graph's forward again from its saved branch
+lengths and differentiates that, so two forwards on one context before a
+backward (as torch.autograd.gradcheck does) give each graph its own
+gradient, never the later forward's.  The context is left holding the
+branch lengths of the graph differentiated last.
 """
 from __future__ import annotations
 
@@ -49,9 +52,18 @@ class BranchLogLik(torch.autograd.Function):
     def backward(fctx, grad_out):
         (t,) = fctx.saved_tensors
         pc = fctx.phylo_ctx
+        lib = N.load()
         g = torch.empty_like(t)
-        pc._check(N.load().phylo_backward_device(pc._ctx, _ptr(g),
-                                                 fctx.generation))
+        rc = lib.phylo_backward_device(pc._ctx, _ptr(g), fctx.generation)
+        if rc == N.PHYLO_ESTATE:
+            # a later pass rewrote the partials: recompute this forward
+            pc.set_branch_lengths(t)
+            out = torch.empty(1, dtype=torch.float64, device=t.device)
+            gen = ctypes.c_uint64(0)
+            pc._check(lib.phylo_forward_device(pc._ctx, _ptr(out),
+                                               ctypes.byref(gen)))
+            rc = lib.phylo_backward_device(pc._ctx, _ptr(g), gen.value)
+        pc._check(rc)
         return grad_out * g * t, None
 
 

@@ -16,13 +16,15 @@
 //    P per branch), so that P v, dP v and P' a all run on the packed FP32
 //    FMA (__ffma2_rn, two lanes per instruction) from 16-byte broadcast
 //    reads;
-//  - the tile's gradient sums are FP32 pairs kept exact with error-free
-//    transformations (converted to FP64 once per tile).
+//  - partials are tile-blocked ([slot][tile][r][32][4], phylo_internal.h),
+//    so each warp's access of one category is 512 contiguous bytes;
+//  - a tile's (warp's) gradient sums are FP32 pairs kept exact with
+//    error-free transformations (converted to FP64 by the final reduction).
 #pragma once
 
 namespace phylo {
 
-constexpr int kP4Threads = kP4TilePatterns;  // patterns per block (one tile)
+constexpr int kP4Threads = 64;  // patterns per block: two tiles
 
 __device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
@@ -140,9 +142,7 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     level_p4_kernel(LevelArgs<float> a) {
   __shared__ P4Mats<RM, PRE, CH> sm;
   __shared__ uint64_t bar;
-  __shared__ F2 red[kP4Threads / 32][2];
-  __shared__ double lred[kP4Threads / 32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int R = EX ? RM : a.n_cat, C = a.n_patterns, S = a.n_states;
   const int4 d = a.level_desc[blockIdx.y];
   const int k = d.x, bi = d.y, bj = d.z;
@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
   const int2 gi2 = hi_ ? a.children[bi] : make_int2(0, 0);  // tips below a cherry
   const int2 gj2 = hj_ ? a.children[bj] : make_int2(0, 0);
   const int c = blockIdx.x * kP4Threads + tid;
+  const int tile = c >> 5;  // this warp's tile
   const bool valid = c < C;
   const uint32_t mbytes = (uint32_t)R * 64;  // one matrix of every category
   const uint32_t cbytes = (PRE ? kP4MatKinds : 1) * mbytes;  // a child's block
@@ -196,14 +197,14 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     if (on && !ci && !hi_)
       vi[r] = bi < a.n_tips ? __ldg(reinterpret_cast<const float4*>(a.tip_partials) + (size_t)bi * C + c)
                             : __ldg(reinterpret_cast<const float4*>(a.post) +
-                                    ((size_t)(bi - a.n_tips) * C + c) * R + r);
+                                    p4_index(bi - a.n_tips, c, r, R, a.n_tiles));
     if (on && !cj && !hj_)
       vj[r] = bj < a.n_tips ? __ldg(reinterpret_cast<const float4*>(a.tip_partials) + (size_t)bj * C + c)
                             : __ldg(reinterpret_cast<const float4*>(a.post) +
-                                    ((size_t)(bj - a.n_tips) * C + c) * R + r);
+                                    p4_index(bj - a.n_tips, c, r, R, a.n_tiles));
     if (PRE && on && k != a.root)
       q[r] = __ldg(reinterpret_cast<const float4*>(a.pre) +
-                   ((size_t)(k - a.n_tips) * C + c) * R + r);
+                   p4_index(k - a.n_tips, c, r, R, a.n_tiles));
   }
   if (PRE && k == a.root) {  // Eq. 4 at the root: q = pi
     const float4 pr = make_float4(a.root_pit[0], S > 1 ? a.root_pit[1] : 0.f,
@@ -267,13 +268,13 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     e += ei + ej;
     if (k != a.root) {
       if (valid) {
-        float4* out = reinterpret_cast<float4*>(a.post) + ((size_t)(k - a.n_tips) * C + c) * R;
+        float4* out = reinterpret_cast<float4*>(a.post) + p4_index(k - a.n_tips, c, 0, R, a.n_tiles);
 #pragma unroll
         for (int r = 0; r < RM; ++r)
           if (r < R) {
             const float2 lo = __fmul2_rn(plo[r], make_float2(f, f));
             const float2 hi = __fmul2_rn(phi[r], make_float2(f, f));
-            out[r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            out[32 * r] = make_float4(lo.x, lo.y, hi.x, hi.y);
           }
         a.escale[(size_t)(k - a.n_tips) * a.escale_stride + c] = e;
       }
@@ -293,13 +294,7 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(kFull, term, o);
-    if (lane == 0) lred[warp] = term;
-    __syncthreads();
-    if (tid == 0) {
-      double l = 0.0;
-      for (int w = 0; w < kP4Threads / 32; ++w) l += lred[w];
-      a.lpart[blockIdx.x] = l;
-    }
+    if (lane == 0 && tile < a.n_tiles) a.lpart[tile] = term;
     return;
   }
   // ---- Eq. 4 and Eq. 8: children's pre-order partials and the ratio ------
@@ -343,26 +338,26 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       float f = 1.f;
       if (!(mi > 0.f) || !isfinite(mi)) atomicOr(a.err, ERR_ZERO_PARTIAL);
       else (void)p4_rescale(mi, f);
-      float4* out = reinterpret_cast<float4*>(a.pre) + ((size_t)(bi - a.n_tips) * C + c) * R;
+      float4* out = reinterpret_cast<float4*>(a.pre) + p4_index(bi - a.n_tips, c, 0, R, a.n_tiles);
 #pragma unroll
       for (int r = 0; r < RM; ++r)
         if (r < R) {
           const float2 lo = __fmul2_rn(qilo[r], make_float2(f, f));
           const float2 hi = __fmul2_rn(qihi[r], make_float2(f, f));
-          out[r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+          out[32 * r] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
     }
     if (int_j) {
       float f = 1.f;
       if (!(mj > 0.f) || !isfinite(mj)) atomicOr(a.err, ERR_ZERO_PARTIAL);
       else (void)p4_rescale(mj, f);
-      float4* out = reinterpret_cast<float4*>(a.pre) + ((size_t)(bj - a.n_tips) * C + c) * R;
+      float4* out = reinterpret_cast<float4*>(a.pre) + p4_index(bj - a.n_tips, c, 0, R, a.n_tiles);
 #pragma unroll
       for (int r = 0; r < RM; ++r)
         if (r < R) {
           const float2 lo = __fmul2_rn(qjlo[r], make_float2(f, f));
           const float2 hi = __fmul2_rn(qjhi[r], make_float2(f, f));
-          out[r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+          out[32 * r] = make_float4(lo.x, lo.y, hi.x, hi.y);
         }
     }
   }
@@ -377,27 +372,16 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
                            __shfl_xor_sync(kFull, other.lo, 16)});
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) mine = f2_add(mine, Acc<float>::shfl_down(mine, o));
-    if (lane == 0) red[warp][0] = mine;
-    if (lane == 16) red[warp][1] = mine;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    gi = red[0][0];
-    gj = red[0][1];
-    for (int w = 1; w < kP4Threads / 32; ++w) {
-      gi = f2_add(gi, red[w][0]);
-      gj = f2_add(gj, red[w][1]);
-    }
     // the pair as stored (the reduction converts to FP64: no FP64 here)
     float2* gp = reinterpret_cast<float2*>(a.gpart);
-    gp[(size_t)bi * a.n_tiles + blockIdx.x] = make_float2(gi.hi, gi.lo);
-    gp[(size_t)bj * a.n_tiles + blockIdx.x] = make_float2(gj.hi, gj.lo);
+    if (tile < a.n_tiles && (lane == 0 || lane == 16))
+      gp[(size_t)(lane == 0 ? bi : bj) * a.n_tiles + tile] = make_float2(mine.hi, mine.lo);
   }
 }
 
 template <int RM, bool EX>
 cudaError_t launch_p4_ex(const LevelArgs<float>& a, bool post, cudaStream_t st) {
-  dim3 grid(a.n_tiles, a.n_level);
+  dim3 grid((a.n_tiles + 1) / 2, a.n_level);
   if (a.level_cherry) {
     if (post) return launch_pdl(level_p4_kernel<RM, EX, false, true>, grid, kP4Threads, 0, st, a);
     return launch_pdl(level_p4_kernel<RM, EX, true, true>, grid, kP4Threads, 0, st, a);

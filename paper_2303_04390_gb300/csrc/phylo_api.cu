@@ -85,7 +85,10 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   const size_t unit = tc ? kTcUnitBytes
                          : (size_t)L.SP * L.SP * L.elem * (p4 ? kP4MatKinds : 1);
   if (!mul_ok(n_br * R, unit, &mat)) return "size overflow";
-  if (!mul_ok(n_int, (size_t)C, &tmp) || !mul_ok(tmp, (size_t)R * L.SP * L.elem, &part))
+  // the FP32 4-state partials are tile-blocked: C padded to whole tiles
+  const size_t c_store =
+      uses_p4_tiles(L.SP, prec == PHYLO_FP64) ? (size_t)L.n_tiles * kP4TilePatterns : (size_t)C;
+  if (!mul_ok(n_int, c_store, &tmp) || !mul_ok(tmp, (size_t)R * L.SP * L.elem, &part))
     return "size overflow";
   bool ok = true;
   ok &= add_region(L, L.children, n_nodes * sizeof(int2));
@@ -107,7 +110,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
     if (!mul_ok(n_int * C, (size_t)R * 16, &tmp)) return "size overflow";
     ok &= add_region(L, L.rterm, tmp);
   }
-  if (!mul_ok((size_t)N, (size_t)round_up(C, 16), &tmp)) return "size overflow";
+  if (!mul_ok((size_t)N, (size_t)tip_state_stride(C), &tmp)) return "size overflow";
   ok &= add_region(L, L.tip_states, tmp);
   if (!mul_ok((size_t)N, (size_t)C, &tmp)) return "size overflow";
   if (flags & PHYLO_FLAG_TIP_PARTIALS) {
@@ -257,7 +260,7 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.pre_escale = ctx->L.pre_escale.bytes ? ctx->dev<int>(ctx->L.pre_escale) : nullptr;
   a.rterm = ctx->L.rterm.bytes ? ctx->dev<void>(ctx->L.rterm) : nullptr;
   a.tip_states = ctx->dev<uint8_t>(ctx->L.tip_states);
-  a.state_stride = round_up(ctx->C, 16);
+  a.state_stride = tip_state_stride(ctx->C);
   a.escale_stride = round_up(ctx->C, 4);
   bool any_partials = false;
   for (int v : ctx->tip_has) any_partials |= v != 0;
@@ -798,7 +801,7 @@ int phylo_set_tip_states(phylo_ctx* ctx, const uint8_t* states) {
                   i / (ctx->C ? ctx->C : 1), i % (ctx->C ? ctx->C : 1),
                   (int)states[i], ctx->S);
   if (n) {  // rows padded to 16 bytes for the bulk copies
-    CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->ws + ctx->L.tip_states.off, round_up(ctx->C, 16),
+    CUDA_TRY(ctx, cudaMemcpy2DAsync(ctx->ws + ctx->L.tip_states.off, tip_state_stride(ctx->C),
                                     states, ctx->C, ctx->C, ctx->N, cudaMemcpyHostToDevice,
                                     ctx->stream),
              "upload tip states");

@@ -56,12 +56,18 @@ constexpr int kBigPatternsF64 = 8;
 constexpr int kBigStatesPerThread = PHYLO_BIG_SPT;  // FP32: states per thread
 constexpr int kMaxStates = 256;
 
-// Patterns per block of the FP32 4-state kernels (kernels_p4.cuh), one
-// thread per pattern.
-#ifndef PHYLO_P4_TILE
-#define PHYLO_P4_TILE 64
-#endif
-constexpr int kP4TilePatterns = PHYLO_P4_TILE;
+// FP32 4-state path (kernels_p4.cuh): one thread per pattern; patterns come
+// in tiles of 32 (one warp), the unit of the partials' layout and of the
+// per-tile sums.  Partials are tile-blocked, [slot][tile][r][32][4] floats,
+// so a warp's access to one category is 512 contiguous bytes.
+constexpr int kP4TilePatterns = 32;
+__host__ __device__ inline size_t p4_index(size_t slot, int c, int r, int R, int n_tiles) {
+  return ((slot * n_tiles + (size_t)(c >> 5)) * R + r) * 32 + (c & 31);
+}
+// Whether a path stores its partials tile-blocked (FP32, 4 padded states).
+inline bool uses_p4_tiles(int SP, bool fp64) { return SP == 4 && !fp64; }
+// Tip-state rows are padded to 16 bytes (row starts aligned for bulk copies).
+inline int tip_state_stride(int C) { return round_up(C, 16); }
 // The FP32 kernels for 4 and 20 padded states read their matrices in the
 // orientations the products use, built that way by the matrix kernel: per
 // branch, [P' of every category][dP' of every category][P of every

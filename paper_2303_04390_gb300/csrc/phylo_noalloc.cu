@@ -82,7 +82,10 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   const bool p4 = uses_tr_layout(L.SP, false);
   const size_t mat = n_br * R * (tc ? kTcUnitBytes
                                     : L.SP * L.SP * sizeof(float) * (p4 ? kP4MatKinds : 1));
-  const size_t part = n_int * (size_t)C * R * L.SP * sizeof(float);
+  // the 4-state partials are tile-blocked: C padded to whole tiles
+  const size_t c_store =
+      uses_p4_tiles(L.SP, false) ? (size_t)L.n_tiles * kP4TilePatterns : (size_t)C;
+  const size_t part = n_int * c_store * R * L.SP * sizeof(float);
   na_add(L, L.children, n_nodes * sizeof(int2));
   na_add(L, L.post_nodes, n_int * sizeof(int));
   na_add(L, L.pre_nodes, n_int * sizeof(int));
@@ -98,7 +101,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
     na_add(L, L.pre_escale, eplane * R);
     na_add(L, L.rterm, n_int * (size_t)C * R * 16);
   }
-  na_add(L, L.tip_states, (size_t)N * round_up(C, 16));
+  na_add(L, L.tip_states, (size_t)N * tip_state_stride(C));
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
   na_add(L, L.Vinv, (size_t)S * S * 8);
@@ -303,7 +306,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
     }
   }
   if (C)
-    NA_TRY(cudaMemcpy2DAsync(ws + L.tip_states.off, round_up(C, 16), tip_states, C, C, N,
+    NA_TRY(cudaMemcpy2DAsync(ws + L.tip_states.off, tip_state_stride(C), tip_states, C, C, N,
                              cudaMemcpyHostToDevice, st),
            "upload tip states");
   NA_TRY(up(L.pattern_w, pattern_weights, (size_t)C * 8), "upload weights");
@@ -367,7 +370,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   a.pre_escale = L.pre_escale.bytes ? reinterpret_cast<int*>(ws + L.pre_escale.off) : nullptr;
   a.rterm = L.rterm.bytes ? static_cast<void*>(ws + L.rterm.off) : nullptr;
   a.tip_states = reinterpret_cast<const uint8_t*>(ws + L.tip_states.off);
-  a.state_stride = round_up(C, 16);
+  a.state_stride = tip_state_stride(C);
   a.escale_stride = round_up(C, 4);
   a.tip_partials = nullptr;
   a.tip_has_partials = nullptr;

@@ -13,8 +13,9 @@ form on two taxa and a substitution route).  An entry that cancels across
 patterns or inside a pattern (|g*| << B) cannot be held to a bound relative
 to |g*| by any finite-precision evaluation -- two FP64 evaluations in
 different but exact orders already differ by ~1e-14 B -- so the bound falls
-back to a fraction of B.  FP32: the measured worst is below 1e-7 B on every
-workload, so 1e-6 B leaves a factor of ten.  FP64: the eigen route of Eq. 1
+back to a fraction of B.  FP32: the measured worst on the full-size
+workloads is 4.6e-7 B (codon-128; hky-1024 1.5e-7 B, aa-256 and mmm-122
+4e-8 B).  FP64: the eigen route of Eq. 1
 leaves an absolute error of order S u sqrt(pi_max / pi_min) in the small
 entries of P (two- and three-nucleotide codon changes on short branches),
 which the 61-state workload turns into ~3e-12 B; the Taylor route of the

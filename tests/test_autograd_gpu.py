@@ -61,34 +61,44 @@ def test_backward_needs_forward():
     assert rc == N.PHYLO_ESTATE
 
 
-def test_two_forwards_then_backward_is_refused():
-    """Two forwards on one context before a backward: the first graph's
-    backward is refused (its partials were overwritten), the second's is
-    right, and re-running the first forward makes its backward right."""
+def test_two_forwards_then_backward():
+    """Two forwards on one context before a backward: the C ABI refuses the
+    first forward's backward (its partials were overwritten), and the
+    autograd Function then recomputes that forward, so each graph gets its
+    own gradient, in either order."""
+    import ctypes
     import paper_2303_04390_gb300 as pg
+    from paper_2303_04390_gb300 import _native as N
     w = synth.small_workload(16, 4, 4, 90, seed=35)
     ctx = pg.from_workload(w, "fp32")
-    lt1 = torch.tensor(np.log(w.t), dtype=torch.float64, device="cuda",
-                       requires_grad=True)
-    lt2 = torch.tensor(np.log(w.t * 1.3), dtype=torch.float64, device="cuda",
-                       requires_grad=True)
-    ll1 = pg.branch_loglik(lt1, ctx)
-    ll2 = pg.branch_loglik(lt2, ctx)
-    with pytest.raises(pg.PhyloError) as e:
-        ll1.backward()
-    assert e.value.code == -4  # PHYLO_ESTATE
-    ll2.backward()
-    ref2 = oracle_eval(w, t=w.t * 1.3)
+    lib = N.load()
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(2 * w.n_tips - 2, dtype=torch.float64, device="cuda")
+    gens = []
+    for scale in (1.0, 1.3):
+        ctx.set_branch_lengths(w.t * scale)
+        gen = ctypes.c_uint64(0)
+        assert lib.phylo_forward_device(ctx._ctx, ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.byref(gen)) == 0
+        gens.append(gen.value)
+    assert gens[1] > gens[0]
+    assert lib.phylo_backward_device(ctx._ctx, ctypes.c_void_p(g.data_ptr()),
+                                     gens[0]) == N.PHYLO_ESTATE
+    assert lib.phylo_backward_device(ctx._ctx, ctypes.c_void_p(g.data_ptr()),
+                                     gens[1]) == 0
     tol = TOL["fp32"]
-    want = ref2[1] * w.t * 1.3
-    bound = np.maximum(tol["g_rel"] * np.abs(want), tol["g_cond"] * ref2[3] * w.t * 1.3)
-    assert np.all(np.abs(lt2.grad.cpu().numpy() - want) <= bound)
-    lt1b = lt1.detach().clone().requires_grad_(True)
-    pg.branch_loglik(lt1b, ctx).backward()
-    ref1 = oracle_eval(w)
-    want = ref1[1] * w.t
-    bound = np.maximum(tol["g_rel"] * np.abs(want), tol["g_cond"] * ref1[3] * w.t)
-    assert np.all(np.abs(lt1b.grad.cpu().numpy() - want) <= bound)
+    for order in ((0, 1), (1, 0)):
+        lts = [torch.tensor(np.log(w.t * s), dtype=torch.float64, device="cuda",
+                            requires_grad=True) for s in (1.0, 1.3)]
+        lls = [pg.branch_loglik(lt, ctx) for lt in lts]
+        for k in order:
+            lls[k].backward()
+        for lt, s in zip(lts, (1.0, 1.3)):
+            ref = oracle_eval(w, t=w.t * s)
+            want = ref[1] * w.t * s
+            bound = np.maximum(tol["g_rel"] * np.abs(want),
+                               tol["g_cond"] * ref[3] * w.t * s)
+            assert np.all(np.abs(lt.grad.cpu().numpy() - want) <= bound), (order, s)
 
 
 def test_forward_backward_agree_with_evaluate_over_steps():
