@@ -43,9 +43,11 @@ struct MatStride { static constexpr int v = SP * SP + 16 / (int)sizeof(T); };
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
+// Load / store a partial vector of SP values as SP/n vector chunks; chunk i
+// sits i * cs vector-widths after the first (cs = 1: contiguous).
 template <typename T, int SP>
 __device__ __forceinline__ void load_vec(const T* __restrict__ src, T (&v)[SP],
-                                         bool active) {
+                                         bool active, int cs = 1) {
   using V = typename Vec<T>::type;
   constexpr int n = Vec<T>::n;
   static_assert(SP % n == 0, "padded states must fill whole vectors");
@@ -53,7 +55,7 @@ __device__ __forceinline__ void load_vec(const T* __restrict__ src, T (&v)[SP],
     const V* s = reinterpret_cast<const V*>(src);
 #pragma unroll
     for (int i = 0; i < SP / n; ++i) {
-      V x = __ldg(s + i);
+      V x = __ldg(s + (size_t)i * cs);
       if constexpr (n == 4) {
         v[4 * i] = x.x; v[4 * i + 1] = x.y; v[4 * i + 2] = x.z; v[4 * i + 3] = x.w;
       } else {
@@ -67,7 +69,7 @@ __device__ __forceinline__ void load_vec(const T* __restrict__ src, T (&v)[SP],
 }
 
 template <typename T, int SP>
-__device__ __forceinline__ void store_vec(T* dst, const T (&v)[SP]) {
+__device__ __forceinline__ void store_vec(T* dst, const T (&v)[SP], int cs = 1) {
   using V = typename Vec<T>::type;
   constexpr int n = Vec<T>::n;
   V* d = reinterpret_cast<V*>(dst);
@@ -79,7 +81,7 @@ __device__ __forceinline__ void store_vec(T* dst, const T (&v)[SP]) {
     } else {
       x.x = v[2 * i]; x.y = v[2 * i + 1];
     }
-    d[i] = x;
+    d[(size_t)i * cs] = x;
   }
 }
 
@@ -113,6 +115,27 @@ __device__ __forceinline__ void matvec_t(const T* __restrict__ M,
 // (uses_tr_layout) and forms every product on the packed FP32 FMA.
 template <typename T, int SP>
 constexpr bool kTrSmall = std::is_same<T, float>::value && SP == 20;
+
+// Where the register kernels keep the partial vector of (slot, pattern c,
+// category r).  FP32 with 20 padded states: tile-blocked by the kernels'
+// block, [slot][tile][chunk][kSmallThreads][4] with tile = c / (threads /
+// RP) and lane (c % (threads / RP)) RP + r, so a warp's access to one
+// 16-byte chunk is 512 contiguous bytes (uses_p20_tiles); chunk stride
+// kSmallThreads float4.  Otherwise pattern-major [slot][c][r][SP].
+template <typename T, int SP, int RP>
+struct SmallVec {
+  static constexpr bool tiled = kTrSmall<T, SP>;
+  static constexpr int cs = tiled ? kSmallThreads : 1;  // chunk stride (vectors)
+  __device__ static size_t offset(size_t slot, int c, int r, int R, int C, int n_tiles) {
+    if constexpr (tiled) {
+      constexpr int CT = kSmallThreads / RP;
+      const size_t tile = slot * n_tiles + c / CT;
+      return tile * (size_t)(kSmallThreads * SP) + (size_t)((c % CT) * RP + r) * 4;
+    } else {
+      return ((slot * C + c) * R + r) * SP;
+    }
+  }
+};
 
 // out[j] = sum_i y[i] X[i][j], two outputs per packed FMA, i in order (the
 // same operations as matvec / matvec_t): X = M' gives M v, X = M gives M' a.
@@ -339,7 +362,7 @@ struct ChildIn {
   int e;    // the child's cumulative exponent (internal child)
 };
 
-template <typename T, int SP>
+template <typename T, int SP, int RP>
 __device__ __forceinline__ void load_child(const LevelArgs<T>& a, int b,
                                            bool compact, int c, int r,
                                            bool active, bool want_e,
@@ -355,7 +378,9 @@ __device__ __forceinline__ void load_child(const LevelArgs<T>& a, int b,
     load_vec<T, SP>(a.tip_partials + ((size_t)b * C + c) * SP, in.v, active);
   } else {
     const size_t slot = (size_t)(b - a.n_tips);
-    load_vec<T, SP>(a.post + ((slot * C + c) * a.n_cat + r) * SP, in.v, active);
+    using SV = SmallVec<T, SP, RP>;
+    load_vec<T, SP>(a.post + SV::offset(slot, c, r, a.n_cat, C, a.n_tiles), in.v, active,
+                    SV::cs);
     if (want_e && active) in.e = a.escale[slot * a.escale_stride + c];
   }
 }
@@ -483,8 +508,8 @@ post_small_kernel(LevelArgs<T> a) {
 #pragma unroll
   for (int u = 0; u < NPT; ++u) {
     if (u < nn) {
-      load_child<T, SP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, true, in[u][0]);
-      load_child<T, SP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, true, in[u][1]);
+      load_child<T, SP, RP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, true, in[u][0]);
+      load_child<T, SP, RP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, true, in[u][1]);
     }
   }
   if (!__syncthreads_and(mbar_wait(&bar, 0))) {
@@ -507,7 +532,8 @@ post_small_kernel(LevelArgs<T> a) {
     if (k != a.root) {
       const size_t slot = (size_t)(k - a.n_tips);
       if (active) {
-        store_vec<T, SP>(a.post + ((slot * C + c) * R + r) * SP, ui);
+        using SV = SmallVec<T, SP, RP>;
+        store_vec<T, SP>(a.post + SV::offset(slot, c, r, R, C, a.n_tiles), ui, SV::cs);
         if (r == 0) a.escale[slot * a.escale_stride + c] = e;
       }
       continue;
@@ -588,11 +614,12 @@ pre_small_kernel(LevelArgs<T> a) {
         for (int s = 0; s < SP; ++s)
           q[u][s] = (active && s < a.n_states) ? (T)a.root_pi[s] : T(0);
       } else {
-        load_vec<T, SP>(a.pre + (((size_t)(k - a.n_tips) * C + c) * R + r) * SP, q[u],
-                        active);
+        using SV = SmallVec<T, SP, RP>;
+        load_vec<T, SP>(a.pre + SV::offset(k - a.n_tips, c, r, R, C, a.n_tiles), q[u], active,
+                        SV::cs);
       }
-      load_child<T, SP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, false, in[u][0]);
-      load_child<T, SP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, false, in[u][1]);
+      load_child<T, SP, RP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, false, in[u][0]);
+      load_child<T, SP, RP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, false, in[u][1]);
     }
   }
   if (!__syncthreads_and(mbar_wait(&bar, 0))) {
@@ -648,8 +675,10 @@ pre_small_kernel(LevelArgs<T> a) {
       else matvec_t<T, SP>(Ri, av, out);
       const T m = pattern_max<T, SP, RP>(out, active);
       rescale<T, SP>(out, m, valid_c, a.err);
-      if (active)
-        store_vec<T, SP>(a.pre + (((size_t)(bi - a.n_tips) * C + c) * R + r) * SP, out);
+      if (active) {
+        using SV = SmallVec<T, SP, RP>;
+        store_vec<T, SP>(a.pre + SV::offset(bi - a.n_tips, c, r, R, C, a.n_tiles), out, SV::cs);
+      }
     }
     if (bj >= a.n_tips) {
       T av[SP], out[SP];
@@ -659,8 +688,10 @@ pre_small_kernel(LevelArgs<T> a) {
       else matvec_t<T, SP>(Rj, av, out);
       const T m = pattern_max<T, SP, RP>(out, active);
       rescale<T, SP>(out, m, valid_c, a.err);
-      if (active)
-        store_vec<T, SP>(a.pre + (((size_t)(bj - a.n_tips) * C + c) * R + r) * SP, out);
+      if (active) {
+        using SV = SmallVec<T, SP, RP>;
+        store_vec<T, SP>(a.pre + SV::offset(bj - a.n_tips, c, r, R, C, a.n_tiles), out, SV::cs);
+      }
     }
     block_sum_acc<T, NT>(gi, gj, red, RP);
     if (threadIdx.x == 0) {

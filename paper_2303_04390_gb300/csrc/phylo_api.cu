@@ -85,11 +85,9 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   const size_t unit = tc ? kTcUnitBytes
                          : (size_t)L.SP * L.SP * L.elem * (p4 ? kP4MatKinds : 1);
   if (!mul_ok(n_br * R, unit, &mat)) return "size overflow";
-  // the FP32 4-state partials are tile-blocked: C padded to whole tiles
-  const size_t c_store =
-      uses_p4_tiles(L.SP, prec == PHYLO_FP64) ? (size_t)L.n_tiles * kP4TilePatterns : (size_t)C;
-  if (!mul_ok(n_int, c_store, &tmp) || !mul_ok(tmp, (size_t)R * L.SP * L.elem, &part))
-    return "size overflow";
+  if (C > (1 << 30)) return "n_patterns too large";
+  const size_t per_node = partial_elems_per_node(L.SP, prec == PHYLO_FP64, C, R, L.n_tiles);
+  if (!mul_ok(n_int, per_node, &tmp) || !mul_ok(tmp, L.elem, &part)) return "size overflow";
   bool ok = true;
   ok &= add_region(L, L.children, n_nodes * sizeof(int2));
   ok &= add_region(L, L.post_nodes, n_int * sizeof(int));

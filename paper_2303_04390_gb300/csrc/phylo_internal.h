@@ -137,6 +137,16 @@ inline int patterns_per_tile(int SP, int R, bool fp64) {
   return fp64 ? kWidePatternsF64 : kWidePatternsF32;
 }
 
+// Partial-vector elements stored per node.  Tile-blocked paths pad the
+// patterns to whole tiles: FP32 with 4 padded states ([tile][r][32][4]),
+// FP32 with 20 padded states ([tile][chunk][kSmallThreads][4], every lane of
+// the RP-wide category slots present); the others store [C][R][SP].
+inline size_t partial_elems_per_node(int SP, bool fp64, int C, int R, int n_tiles) {
+  if (uses_p4_tiles(SP, fp64)) return (size_t)n_tiles * kP4TilePatterns * R * SP;
+  if (SP == 20 && !fp64) return (size_t)n_tiles * kSmallThreads * SP;
+  return (size_t)C * R * SP;
+}
+
 // Arguments of the post- and pre-order level kernels.  All arrays live in
 // the caller's workspace.  Partials are pattern-major: [slot][c][r][SP],
 // slot = node - n_tips for internal nodes.

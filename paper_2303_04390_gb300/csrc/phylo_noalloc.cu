@@ -82,10 +82,8 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   const bool p4 = uses_tr_layout(L.SP, false);
   const size_t mat = n_br * R * (tc ? kTcUnitBytes
                                     : L.SP * L.SP * sizeof(float) * (p4 ? kP4MatKinds : 1));
-  // the 4-state partials are tile-blocked: C padded to whole tiles
-  const size_t c_store =
-      uses_p4_tiles(L.SP, false) ? (size_t)L.n_tiles * kP4TilePatterns : (size_t)C;
-  const size_t part = n_int * c_store * R * L.SP * sizeof(float);
+  const size_t part =
+      n_int * partial_elems_per_node(L.SP, false, C, R, L.n_tiles) * sizeof(float);
   na_add(L, L.children, n_nodes * sizeof(int2));
   na_add(L, L.post_nodes, n_int * sizeof(int));
   na_add(L, L.pre_nodes, n_int * sizeof(int));
