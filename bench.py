@@ -359,12 +359,21 @@ def kernel_source_hash():
 
 
 def run_served(args, seed=0):
-    """Served stream: requests drawn from a pool of distinct seeded
-    problems (Yule trees with 16-2,048 taxa, 100-20,000 patterns, 4 or 20
-    states), first all at once (closed loop, to measure throughput mu),
-    then as a Poisson stream at 0.7 mu."""
+    """Served streams over a pool of distinct seeded problems (Yule trees
+    with 16-2,048 taxa, 100-20,000 patterns, 4 or 20 states):
+      one-shot  -- every request a new problem: first all at once (closed
+                   loop, throughput mu), then a Poisson stream at 0.7 mu;
+      sessions  -- HMC-like chains, each a session on one problem whose
+                   next step (new branch lengths) is submitted when the
+                   previous result returns; the context stays resident.
+    Beside them, the requests' device times measured alone, one at a time
+    (their sum over the one-shot stream's elapsed time says how much the
+    concurrent streams overlap)."""
+    import numpy as np
     import synth
-    from paper_2303_04390_gb300.serve import (Server, latency_summary,
+    import torch
+    import paper_2303_04390_gb300 as pg
+    from paper_2303_04390_gb300.serve import (Request, Server, latency_summary,
                                               poisson_arrivals)
     pool = [synth.served_request(k, seed) for k in range(args.serve_pool)]
     n = args.serve_requests
@@ -381,8 +390,54 @@ def run_served(args, seed=0):
     arrivals = poisson_arrivals(n, rate, seed=seed + 1)
     t0 = time.perf_counter()
     res = srv.run(reqs, arrivals)
-    open_loop = latency_summary(res, time.perf_counter() - t0)
+    open_s = time.perf_counter() - t0
+    open_loop = latency_summary(res, open_s)
+    # -- sessions: closed-loop chains, each submitting its next step ------
+    n_chains = min(args.serve_chains, len(pool))
+    n_steps = args.serve_chain_steps
+    rng = np.random.default_rng(seed + 2)
+    owner, done = {}, [0] * n_chains
+
+    def step_t(k):
+        w = pool[k]
+        return w.t * np.exp(0.05 * rng.standard_normal(w.t.shape))
+
+    def follow(rid, result):
+        k = owner[rid]
+        done[k] += 1
+        if done[k] < n_steps:
+            owner[len(owner)] = k
+            return Request(pool[k], t=step_t(k), session=k)
+        return None
+
+    first = []
+    for k in range(n_chains):
+        owner[k] = k
+        first.append(Request(pool[k], t=step_t(k), session=k))
+    srv.run(first[:n_chains])  # set the sessions up (not timed)
+    owner, done = {k: k for k in range(n_chains)}, [0] * n_chains
+    first = [Request(pool[k], t=step_t(k), session=k) for k in range(n_chains)]
+    t0 = time.perf_counter()
+    res_s = srv.run(first, follow_up=follow)
+    sessions = latency_summary(res_s, time.perf_counter() - t0)
+    hits = sum(r.session_hit for r in res_s)
+    peak_used, peak_active = srv.admission.peak_used, srv.admission.peak_active
+    evictions = srv.evictions  # (close() below releases the sessions)
     srv.close()
+    # -- device time of each problem alone (graph replay, events) ---------
+    alone_ms = []
+    for w in pool:
+        ctx = pg.from_workload(w, "fp32")
+        ctx.evaluate_device()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            ctx.evaluate_device()
+        e1.record()
+        torch.cuda.synchronize()
+        alone_ms.append(e0.elapsed_time(e1) / 3)
+        ctx.close()
+    alone_sum_s = sum(alone_ms[k % len(pool)] for k in range(n)) / 1e3
     return {
         "requests": n, "distinct_problems": len(pool),
         "arrival": f"Poisson at 0.7 x closed-loop throughput "
@@ -393,9 +448,20 @@ def run_served(args, seed=0):
         "closed_loop_evals_per_s": closed["evals_per_s"],
         "closed_loop_p50_ms": closed["p50_ms"],
         "closed_loop_p99_ms": closed["p99_ms"],
+        "device_s_alone_sum": alone_sum_s,
+        "open_loop_elapsed_s": open_s,
+        "sessions": {
+            "chains": n_chains, "steps_per_chain": n_steps,
+            "arrival": "closed loop per chain: the next step (new branch "
+                       "lengths) is submitted when the previous result returns",
+            "evals_per_s": sessions["evals_per_s"], "p50_ms": sessions["p50_ms"],
+            "p99_ms": sessions["p99_ms"], "max_ms": sessions["max_ms"],
+            "failed": sessions["failed"], "session_hits": hits,
+            "evictions": evictions,
+        },
         "budget_gb": args.serve_budget_gb,
-        "peak_resident_gb": srv.admission.peak_used / (1 << 30),
-        "peak_active": srv.admission.peak_active,
+        "peak_resident_gb": peak_used / (1 << 30),
+        "peak_active": peak_active,
     }
 
 
@@ -758,6 +824,9 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-pool", type=int, default=96)
     ap.add_argument("--serve-budget-gb", type=float, default=32.0)
+    ap.add_argument("--serve-chains", type=int, default=64,
+                    help="sessions (HMC-like chains) in the session stream")
+    ap.add_argument("--serve-chain-steps", type=int, default=16)
     ap.add_argument("--profile", action="store_true",
                     help="run warm-up + K evaluations only (profiler target)")
     args = ap.parse_args()
