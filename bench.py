@@ -572,6 +572,11 @@ def rooflines(w, precision, phase_ms, level_counts, peaks, n_sm, workload):
         kernels = {"pmat": "pmat_tc_kernel", "post": "post_tc_pipe_kernel",
                    "pre": "pre_tc_kernel + ratio_tc_kernel",
                    "reduce": "reduce_kernel"}
+    if precision == "fp32" and 64 < w.n_states <= 128:
+        kernels = {"pmat": "pmat_big_df_kernel + tcb_tiles_kernel",
+                   "post": "post_tcb_kernel + root_tcb_kernel",
+                   "pre": "pre_tcb_a_kernel + pre_tcb_b_kernel + ratio_tc_kernel",
+                   "reduce": "reduce_kernel"}
     phases = {}
     for n_, ms_ in zip(names, phase_ms):
         phases[n_] = {"ms": ms_, "algorithmic_bytes": by[n_],
@@ -600,7 +605,8 @@ def rooflines(w, precision, phase_ms, level_counts, peaks, n_sm, workload):
         roofline["alu"] = {"achieved": aach, "peak": alu_peak, "unit": "TFLOP/s",
                            "frac": aach / alu_peak, "peak_kind": alu_kind,
                            "algorithmic_flops_per_launch": fl[dom] / n_launch_dom}
-    if w.n_states > 64:
+    tensor_path = precision == "fp32" and 20 < w.n_states <= 128
+    if w.n_states > 64 and not tensor_path:
         if precision == "fp32":
             apeak, akind = alu_peak, alu_kind
         else:
@@ -618,7 +624,7 @@ def rooflines(w, precision, phase_ms, level_counts, peaks, n_sm, workload):
                     "algorithmic_bytes_per_launch": by[dom] / n_launch_dom},
         }
     tensor = None
-    if precision == "fp32" and 20 < w.n_states <= 64:
+    if tensor_path:
         tpeak = peaks.get("bf16_tflops_sustained")
         tkind = "measured" if tpeak else "fallback"
         tpeak = tpeak or 1700.0

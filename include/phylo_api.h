@@ -222,8 +222,10 @@ int phylo_launches_per_evaluation(const phylo_ctx* ctx);
 
 /* Length of the level schedule: the number of post-order launches (tree
  * height, less the heights left empty by fused cherries on the FP32
- * 4-state path) and of pre-order launches (distinct depths of internal
- * nodes).  Both 0 before the tree is set. */
+ * 4-state path; plus one for Eq. 3 at the root on the FP32 path for 65-128
+ * states) and of pre-order launches (distinct depths of internal nodes;
+ * twice that on the FP32 path for 65-128 states, which runs two kernels per
+ * level).  Both 0 before the tree is set. */
 int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
                        int* n_pre_levels);
 

@@ -19,7 +19,7 @@ LIB = os.path.join(PKG, "libphylograd.so")
 SOURCES = ["phylo_api.cu", "kernels_fp32.cu", "kernels_fp64.cu",
            "phylo_noalloc.cu"]
 HEADERS = ["phylo_internal.h", "kernels.cuh", "kernels_big.cuh", "kernels_p4.cuh",
-           "kernels_tc64.cuh", "tc.cuh", "tma.cuh"]
+           "kernels_tc64.cuh", "kernels_tcb.cuh", "tc.cuh", "tma.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-Wall"]

@@ -1068,6 +1068,7 @@ inline size_t wide_pre_smem(int R) {
 #include "kernels_p4.cuh"
 #include "kernels_tc64.cuh"
 #include "kernels_big.cuh"
+#include "kernels_tcb.cuh"
 
 namespace phylo {
 
@@ -1154,7 +1155,9 @@ cudaError_t launch_level_impl(const LevelArgs<T>& a, int SP, int RP, bool post,
         return launch_pdl(pre_wide_kernel<T>, grid, kWideThreads, wide_pre_smem<T>(a.n_cat), st,
                           a);
       }
-    case 128: return launch_big<T, 128>(a, post, st);
+    case 128:
+      if constexpr (std::is_same<T, float>::value) return launch_tcb(a, post, st);
+      else return launch_big<T, 128>(a, post, st);
     case 256: return launch_big<T, 256>(a, post, st);
     default: return cudaErrorInvalidValue;
   }
@@ -1177,7 +1180,10 @@ cudaError_t prepare_impl(int SP, int RP) {
                                   (int)wide_pre_smem<T>(8));
     }
   }
-  if (SP == 128) return prepare_big<T, 128>();
+  if (SP == 128) {
+    if constexpr (std::is_same<T, float>::value) return prepare_tcb();
+    else return prepare_big<T, 128>();
+  }
   if (SP == 256) return prepare_big<T, 256>();
   return cudaSuccess;
 }
@@ -1204,7 +1210,7 @@ cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
       else pmat_kernel<T, 64><<<units, 256, 0, st>>>(a);
       break;
     case 128:
-      if constexpr (std::is_same<T, float>::value) return launch_pmat_big<128>(a, st);
+      if constexpr (std::is_same<T, float>::value) return launch_pmat_tcb(a, st);
       else pmat_kernel<T, 128><<<units, 256, 0, st>>>(a);
       break;
     case 256:
@@ -1219,7 +1225,7 @@ cudaError_t launch_pmat_impl(const PmatArgs& a, int SP, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_pre_finish_impl(const LevelArgs<T>& a, int SP, cudaStream_t st) {
   if constexpr (std::is_same<T, float>::value) {
-    if (SP == 64) return launch_ratio_tc64(a, st);
+    if (SP == 64 || SP == 128) return launch_ratio_tc64(a, st);
   }
   return cudaSuccess;
 }

@@ -1,0 +1,560 @@
+// FP32 kernels for 65..128 states (S_pad = 128: the paper's 122-state
+// Markov-modulated codon model) on the tensor cores, K- and N-tiled.
+//
+// Arithmetic as on the 64-state tensor-core path (kernels_tc64.cuh), per
+// (node, tile of 128 patterns, category r):
+//   post:    U_x = p_x P_x'                       (both children)
+//            p_k = U_i o U_j, rescaled
+//   pre (A): [U_x | V_x] = p_x [P_x ; dP_x]'      (both children)
+//            a_i = q_k o U_j,  a_j = q_k o U_i
+//            num_x = a_x . V_x,  den = a_i . U_i   -> per-category Eq. 8 terms
+//            a_x written into the q slot of each internal child
+//   pre (B): q_x = a_x P_x, rescaled in place     (internal children)
+// With 128 padded states every operand is cut into 64 x 64 blocks: a
+// contraction D[128 x 128] = A[128 x 128] B[128 x 128]' is, for each of the
+// two 64-column blocks of D, two MMA groups of K = 64 accumulated in TMEM.
+// Each group is the BF16 x3 split of tc.cuh (six products per FP32
+// product), so results carry FP32 accuracy.  Partial tiles are split into
+// their three BF16 terms in shared memory (the A operand, one 64-column
+// K-block at a time); the matrix blocks come pre-split from
+// tcb_tiles_kernel and are bulk-copied (cp.async.bulk).  A and B buffers
+// are double-buffered, so one round's loads and splits overlap the previous
+// round's MMAs.  A compact tip child enters the MMA as its one-hot (or, for
+// a gap, all-ones) rows, so every child takes the same path.
+//
+// TMEM: post 256 columns [U_i | U_j]; pre (A) 512 [U_i | V_i | U_j | V_j];
+// pre (B) 128 [q_x].  One CTA per SM (192 KB of shared memory).
+//
+// Rescaling, exponents and the Eq. 8 terms follow the 64-state path
+// (per-category exponents; ratio_tc_kernel combines the categories); the
+// root's post-order CTAs store p_root and root_tcb_kernel forms log L_c.
+// Every wait is bounded; on expiry the kernel raises ERR_TIMEOUT, drains
+// (bounded) the copies and MMAs it issued, frees its TMEM and returns.
+#pragma once
+
+namespace phylo {
+
+constexpr int kTcbSP = 128;                  // padded states of this path
+constexpr int kTcbNB = kTcbSP / 64;          // 64-blocks per dimension
+constexpr uint32_t kTcbBlock = 3 * kTerm64;  // one 64 x 64 three-term block
+static_assert(kTcbUnitBytes == 3 * kTcbNB * kTcbNB * kTcbBlock, "tile block size");
+// Shared memory: A ring 2 x 48 KB, B ring 2 x 48 KB (+1024 for alignment).
+constexpr size_t kTcbSmem = 1024 + 2 * (size_t)kOp128 + 4 * (size_t)kTcbBlock;
+constexpr int kTcbLd = kTcbSP + 4;           // output staging row stride (floats)
+static_assert((size_t)kTcRows * kTcbLd * 4 <= 2 * (size_t)kOp128, "staging fits in A");
+
+// Offset of block (kind, jn, jk) in a (branch, category) unit of tiles:
+// kind 0 = P, 1 = dP, 2 = P' (its rows are the columns of P); block row n,
+// column k holds M[64 jn + n][64 jk + k].  The blocks of one K-block jk are
+// adjacent (jn fastest), so one bulk copy stages a round's B operand.
+__host__ __device__ constexpr size_t tcb_block(int kind, int jn, int jk) {
+  return (((size_t)kind * kTcbNB + jk) * kTcbNB + jn) * kTcbBlock;
+}
+
+// Pre-split matrix blocks of every (branch, category) from the FP32 P and dP
+// of the matrix kernel: one CTA per block, thread n writes block row n.
+template <typename T>  // float only (a template: the header is in two units)
+__global__ void __launch_bounds__(64) tcb_tiles_kernel(const T* __restrict__ P,
+                                                       const T* __restrict__ D,
+                                                       unsigned char* __restrict__ tiles) {
+  constexpr int NBLK = 3 * kTcbNB * kTcbNB;
+  const int unit = blockIdx.x / NBLK, blk = blockIdx.x % NBLK;
+  const int kind = blk / (kTcbNB * kTcbNB), jn = (blk / kTcbNB) % kTcbNB, jk = blk % kTcbNB;
+  const T* M = (kind == 1 ? D : P) + (size_t)unit * kTcbSP * kTcbSP;
+  unsigned char* out = tiles + (size_t)unit * kTcbUnitBytes + tcb_block(kind, jn, jk);
+  const int n = threadIdx.x, nn = 64 * jn + n;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int kk = 64 * jk + 8 * j + i;
+      x[i] = kind == 2 ? M[(size_t)kk * kTcbSP + nn] : M[(size_t)nn * kTcbSP + kk];
+    }
+    tc::put_split3(out, out + kTerm64, out + 2 * kTerm64, n, j, x);
+  }
+}
+
+// First row (pattern 0, category r) of a non-compact child's partials on
+// this path and the row stride, in floats.
+__device__ __forceinline__ const float* tcb_child_base(const LevelArgs<float>& a,
+                                                       const TcChild& x, int r, size_t* stride) {
+  const int C = a.n_patterns;
+  if (x.internal) {
+    *stride = (size_t)a.n_cat * kTcbSP;
+    return a.post + ((size_t)(x.b - a.n_tips) * C * a.n_cat + r) * kTcbSP;
+  }
+  *stride = kTcbSP;
+  return a.tip_partials + (size_t)x.b * C * kTcbSP;
+}
+
+__device__ __forceinline__ const unsigned char* tcb_unit(const LevelArgs<float>& a, int b,
+                                                         int r) {
+  return a.tc_tiles + ((size_t)b * a.n_cat + r) * kTcbUnitBytes;
+}
+
+// Fill the A operand with K-block kb (states 64 kb .. 64 kb + 63) of a
+// child's rows: its partials, or for a compact tip its one-hot rows (all
+// ones up to S for a gap; zero rows past the last pattern).
+__device__ __forceinline__ void tcb_fill_a(unsigned char* A, const LevelArgs<float>& a,
+                                           const TcChild& x, const float* src, size_t stride,
+                                           int kb, int c0) {
+  const int C = a.n_patterns, S = a.n_states;
+  if (!x.compact) {
+    float4 v[8];
+    coop_load(v, src + 64 * kb, stride, c0, C);
+    coop_put(A, v);
+    return;
+  }
+  const int j = threadIdx.x & 7;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int m = coop_row(it), c = c0 + m;
+    const int y = c < C ? (int)a.tip_states[(size_t)x.b * a.state_stride + c] : -1;
+    float v8[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int kk = 64 * kb + 8 * j + i;
+      v8[i] = y < 0 ? 0.f : y < S ? (kk == y ? 1.f : 0.f) : (kk < S ? 1.f : 0.f);
+    }
+    tc::put_split3(A, A + kTerm128, A + 2 * kTerm128, m, j, v8);
+  }
+}
+
+// D (+)= A B' for the two 64-column blocks jn of one K-block (the MMAs of
+// one round): B holds the two blocks (jn = 0, 1) back to back.
+__device__ __forceinline__ void tcb_mma_round(uint32_t d_tmem, const unsigned char* A,
+                                              const unsigned char* B, bool accumulate) {
+  uint32_t ta[3];
+  term_addrs(A, kTerm128, ta);
+#pragma unroll
+  for (int jn = 0; jn < kTcbNB; ++jn) {
+    uint32_t tb[3];
+    term_addrs(B + jn * kTcbBlock, kTerm64, tb);
+    tc::mma_split_bf16x3_acc<64>(d_tmem + 64 * jn, ta, tb, accumulate);
+  }
+}
+
+// Coalesced store of staged 128-float rows (a quarter warp writes one
+// 128-byte quarter row per instruction).
+__device__ __forceinline__ void tcb_store_rows(float* __restrict__ base, size_t stride, int c0,
+                                               int C, const float* st) {
+  const int jj = threadIdx.x & 7;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int row = coop_row(it), c = c0 + row;
+    if (c < C) {
+      float* dst = base + (size_t)c * stride;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<float4*>(dst + 32 * q + 4 * jj) =
+            *reinterpret_cast<const float4*>(st + row * kTcbLd + 32 * q + 4 * jj);
+    }
+  }
+}
+
+// Bookkeeping of the asynchronous phases a CTA has issued and waited on,
+// so that a timeout can drain what is still in flight.
+struct TcbPhases {
+  uint32_t issued[4], waited[4];  // bars: tma 0, tma 1, mma 0, mma 1
+};
+
+__device__ __forceinline__ bool tcb_wait(uint64_t* bar, TcbPhases& ph, int i, int* err) {
+  const bool mine = mbar_wait(bar, ph.waited[i] & 1);
+  const bool ok = __syncthreads_and(mine);
+  if (ok) ++ph.waited[i];
+  else if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
+  tc::fence_after();
+  return ok;
+}
+
+__device__ __forceinline__ void tcb_drain(uint64_t* bars, const TcbPhases& ph) {
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 4; ++i)
+      for (uint32_t p = ph.waited[i]; p < ph.issued[i]; ++p) (void)mbar_wait(&bars[i], p & 1);
+}
+
+// Common prologue: barriers, TMEM, the block's row and half.
+#define TCB_PROLOGUE(COLS)                                                   \
+  extern __shared__ unsigned char smraw[];                                   \
+  unsigned char* base = align1024(smraw);                                    \
+  unsigned char* A[2] = {base, base + kOp128};                               \
+  unsigned char* B[2] = {base + 2 * kOp128, base + 2 * kOp128 + 2 * kTcbBlock}; \
+  __shared__ uint64_t bars[4]; /* tma 0, tma 1, mma 0, mma 1 */              \
+  __shared__ uint32_t tmem_slot;                                             \
+  const int tid = threadIdx.x, warp = tid >> 5;                              \
+  const int row = tid & (kTcRows - 1), h = tid / kTcRows;                    \
+  if (warp == 0) tc::alloc(&tmem_slot, COLS);                                \
+  if (tid == 0)                                                              \
+    for (int i = 0; i < 4; ++i) mbar_init_fenced(&bars[i], 1);               \
+  __syncthreads();                                                           \
+  tc::fence_after();                                                         \
+  const uint32_t tmem = tmem_slot;                                           \
+  const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);          \
+  TcbPhases ph = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+
+#define TCB_EPILOGUE(COLS)                                                   \
+  tcb_drain(bars, ph);                                                       \
+  tc::fence_before();                                                        \
+  __syncthreads();                                                           \
+  if (warp == 0) tc::dealloc(tmem, COLS);
+
+// One round of a contraction: copy the two B blocks at `bsrc` (blocks jn =
+// 0, 1 of one kind and K-block) into buffer b, optionally refill A buffer
+// `ab` with K-block kb of a child's rows, then (thread 0) issue the round's
+// MMAs into d_tmem once the copies have landed.
+__device__ __forceinline__ bool tcb_round(unsigned char* const (&A)[2],
+                                          unsigned char* const (&B)[2], uint64_t* bars,
+                                          TcbPhases& ph, int b, const unsigned char* bsrc,
+                                          bool fill, int ab, const LevelArgs<float>& a,
+                                          const TcChild& x, const float* src, size_t stride,
+                                          int kb, int c0, uint32_t d_tmem, bool accumulate) {
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bars[b], 2 * kTcbBlock);
+    ++ph.issued[b];
+    bulk_g2s(B[b], bsrc, 2 * kTcbBlock, &bars[b]);
+  }
+  if (fill) tcb_fill_a(A[ab], a, x, src, stride, kb, c0);
+  tc::fence_smem_for_async();
+  if (!tcb_wait(&bars[b], ph, b, a.err)) return false;
+  if (threadIdx.x == 0) {
+    tcb_mma_round(d_tmem, A[ab], B[b], accumulate);
+    tc::commit(&bars[2 + b]);
+    ++ph.issued[2 + b];
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Post-order level (Eq. 2); the root's p is stored like any other and
+// root_tcb_kernel forms Eq. 3.
+// ---------------------------------------------------------------------------
+template <typename T>  // float only
+__global__ void __launch_bounds__(kTcThreads) post_tcb_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();  // before TMEM, smem or any global access
+  TCB_PROLOGUE(256)
+  __shared__ float xch[2][kTcRows];
+  const int R = a.n_cat, C = a.n_patterns;
+  const int4 d = a.level_desc[blockIdx.y];
+  const int k = d.x;
+  const TcChild xs[2] = {tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0),
+                         tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1)};
+  const int c0 = blockIdx.x * kTcRows, c = c0 + row;
+  const bool valid = c < C;
+  const int r = blockIdx.z, estr = a.escale_stride;
+  int E = 0;
+  if (valid)
+    for (int x = 0; x < 2; ++x)
+      if (xs[x].internal) E += a.escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c];
+  bool ok = true;
+  // rounds i = (child x, K-block kb): U_x (+)= p_x[:, kb] P_x[:, kb]'
+  for (int i = 0; i < 2 * kTcbNB && ok; ++i) {
+    const int x = i / kTcbNB, kb = i % kTcbNB, b = i & 1;
+    if (i >= 2 && !(ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err))) break;  // round i-2
+    size_t stride = 0;
+    const float* src = xs[x].compact ? nullptr : tcb_child_base(a, xs[x], r, &stride);
+    ok = tcb_round(A, B, bars, ph, b, tcb_unit(a, xs[x].b, r) + tcb_block(0, 0, kb), true, b,
+                   a, xs[x], src, stride, kb, c0, tmem + 128 * x, kb > 0);
+  }
+  for (int b = 0; b < 2 && ok; ++b) ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err);
+  if (ok) {
+    // epilogue: p = U_i o U_j on this half row, the row max, scale, store
+    float p[64];
+    float m = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float ui[32], uj[32];
+      tc::ld32(trow + 0 + 64 * h + 32 * q, ui);
+      tc::ld32(trow + 128 + 64 * h + 32 * q, uj);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        p[32 * q + i] = ui[i] * uj[i];
+        m = fmaxf(m, fabsf(p[32 * q + i]));
+      }
+    }
+    xch[h][row] = m;
+    __syncthreads();
+    m = fmaxf(m, xch[1 - h][row]);
+    // an all-zero vector is legitimate for one category; the root's
+    // log-likelihood kernel flags a pattern whose categories all vanish
+    int e = 0;
+    if (valid) {
+      if (!isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else if (m > 0.f) (void)frexpf(m, &e);
+      e = max(e, -126);  // 2^-e stays finite for a subnormal maximum
+    }
+    const float f = ldexpf(1.f, -e);
+    float* st = reinterpret_cast<float*>(base);  // A is free: every MMA is done
+#pragma unroll
+    for (int i = 0; i < 64; i += 4)
+      *reinterpret_cast<float4*>(st + row * kTcbLd + 64 * h + i) =
+          make_float4(p[i] * f, p[i + 1] * f, p[i + 2] * f, p[i + 3] * f);
+    const size_t kslot = (size_t)(k - a.n_tips);
+    if (valid && h == 0) a.escale[(kslot * R + r) * estr + c] = E + e;
+    __syncthreads();
+    tcb_store_rows(a.post + (kslot * C * R + r) * kTcbSP, (size_t)R * kTcbSP, c0, C, st);
+  }
+  TCB_EPILOGUE(256)
+}
+
+// ---------------------------------------------------------------------------
+// Eq. 3 at the root: L_c = sum_r w_r 2^{E_r} pi' p_root,r,c, the sum over r
+// taken relative to the largest exponent; W_c log L_c summed per tile.
+// ---------------------------------------------------------------------------
+template <typename T>  // float only
+__global__ void __launch_bounds__(kTcRows) root_tcb_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();
+  __shared__ double lred[kTcRows / 32];
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int c = blockIdx.x * kTcRows + threadIdx.x;
+  const size_t rslot = (size_t)(a.root - a.n_tips);
+  double term = 0.0;
+  if (c < C) {
+    float lsum = 0.f;
+    int lexp = INT_MIN / 2;
+    for (int r = 0; r < R; ++r) {
+      const float4* p = reinterpret_cast<const float4*>(
+          a.post + ((rslot * C + c) * R + r) * kTcbSP);
+      float pd = 0.f;
+      for (int s4 = 0; s4 < (S + 3) / 4; ++s4) {
+        const float4 v = p[s4];
+        const int s = 4 * s4;
+        pd = fmaf(a.root_pit[s], v.x, pd);
+        if (s + 1 < S) pd = fmaf(a.root_pit[s + 1], v.y, pd);
+        if (s + 2 < S) pd = fmaf(a.root_pit[s + 2], v.z, pd);
+        if (s + 3 < S) pd = fmaf(a.root_pit[s + 3], v.w, pd);
+      }
+      if (pd == 0.f) continue;
+      const int E = a.escale[(rslot * R + r) * a.escale_stride + c];
+      const float t = a.cat_wt[r] * pd;
+      if (E > lexp) {
+        lsum = lsum * pow2i(lexp - E) + t;
+        lexp = E;
+      } else {
+        lsum += t * pow2i(E - lexp);
+      }
+    }
+    if (!(lsum > 0.f) || !isfinite(lsum)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+    else term = (double)a.pattern_wt[c] * (log((double)lsum) + (double)lexp * 0.69314718055994530942);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(kFull, term, o);
+  if ((threadIdx.x & 31) == 0) lred[threadIdx.x >> 5] = term;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double l = 0.0;
+    for (int w = 0; w < kTcRows / 32; ++w) l += lred[w];
+    a.lpart[blockIdx.x] = l;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Pre-order level, part A: [U_x | V_x], the Eq. 8 terms, a_x
+// ---------------------------------------------------------------------------
+template <typename T>  // float only
+__global__ void __launch_bounds__(kTcThreads) pre_tcb_a_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();
+  TCB_PROLOGUE(512)
+  __shared__ float xch[2][3][kTcRows];
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int4 d = a.level_desc[blockIdx.y];
+  const int k = d.x;
+  const TcChild xs[2] = {tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0),
+                         tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1)};
+  const int c0 = blockIdx.x * kTcRows, c = c0 + row;
+  const bool valid = c < C;
+  const int r = blockIdx.z, estr = a.escale_stride;
+  const bool root = k == a.root;
+  const size_t kslot = (size_t)(k - a.n_tips);
+  int eq_k = 0, ep[2] = {0, 0};
+  bool gap[2] = {false, false};
+  if (valid) {
+    if (!root) eq_k = a.pre_escale[(kslot * R + r) * estr + c];
+    for (int x = 0; x < 2; ++x) {
+      if (xs[x].internal) ep[x] = a.escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c];
+      if (xs[x].compact) gap[x] = (int)a.tip_states[(size_t)xs[x].b * a.state_stride + c] >= S;
+    }
+  }
+  bool ok = true;
+  // rounds i = (child x, K-block kb, kind m in {P, dP}); A refilled when the
+  // K-block changes: [U_x | V_x] (+)= p_x[:, kb] [P_x ; dP_x][:, kb]'
+  for (int i = 0; i < 4 * kTcbNB && ok; ++i) {
+    const int x = i / (2 * kTcbNB), kb = (i / 2) % kTcbNB, m = i & 1, b = i & 1;
+    if (i >= 2 && !(ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err))) break;  // round i-2
+    size_t stride = 0;
+    const float* src = xs[x].compact ? nullptr : tcb_child_base(a, xs[x], r, &stride);
+    ok = tcb_round(A, B, bars, ph, b, tcb_unit(a, xs[x].b, r) + tcb_block(m, 0, kb), m == 0,
+                   (i / 2) & 1, a, xs[x], src, stride, kb, c0, tmem + 256 * x + 128 * m, kb > 0);
+  }
+  for (int b = 0; b < 2 && ok; ++b) ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err);
+  if (ok) {
+    // epilogue: per 16 columns of this half row
+    float ni = 0.f, nj = 0.f, dn = 0.f;
+    const float* qrow = a.pre + ((kslot * C + c) * R + r) * kTcbSP;
+    float* ai_out = xs[0].internal
+                        ? a.pre + (((size_t)(xs[0].b - a.n_tips) * C + c) * R + r) * kTcbSP
+                        : nullptr;
+    float* aj_out = xs[1].internal
+                        ? a.pre + (((size_t)(xs[1].b - a.n_tips) * C + c) * R + r) * kTcbSP
+                        : nullptr;
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const int s0 = 64 * h + 16 * q;
+      float ui[16], vi[16], uj[16], vj[16], qv[16];
+      tc::ld16(trow + 0 + s0, ui);
+      tc::ld16(trow + 128 + s0, vi);
+      tc::ld16(trow + 256 + s0, uj);
+      tc::ld16(trow + 384 + s0, vj);
+      if (root) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) qv[i] = s0 + i < S ? a.root_pit[s0 + i] : 0.f;
+      } else if (valid) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) {
+          const float4 t4 = *reinterpret_cast<const float4*>(qrow + s0 + i);
+          qv[i] = t4.x; qv[i + 1] = t4.y; qv[i + 2] = t4.z; qv[i + 3] = t4.w;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) qv[i] = 0.f;
+      }
+      float ai[16], aj[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        ai[i] = qv[i] * uj[i];  // a_i = q o U_j
+        aj[i] = qv[i] * ui[i];  // a_j = q o U_i
+        dn = fmaf(ai[i], ui[i], dn);
+        // a gap's d/dt of the all-ones vector is 0
+        if (!gap[0]) ni = fmaf(ai[i], vi[i], ni);
+        if (!gap[1]) nj = fmaf(aj[i], vj[i], nj);
+      }
+      if (valid) {
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) {
+          if (ai_out)
+            *reinterpret_cast<float4*>(ai_out + s0 + i) =
+                make_float4(ai[i], ai[i + 1], ai[i + 2], ai[i + 3]);
+          if (aj_out)
+            *reinterpret_cast<float4*>(aj_out + s0 + i) =
+                make_float4(aj[i], aj[i + 1], aj[i + 2], aj[i + 3]);
+        }
+      }
+    }
+    xch[h][0][row] = ni;
+    xch[h][1][row] = nj;
+    xch[h][2][row] = dn;
+    __syncthreads();
+    if (valid && h == 0) {
+      const float w = a.cat_wt[r];
+      reinterpret_cast<float4*>(a.rterm)[(kslot * C + c) * R + r] =
+          make_float4(w * (ni + xch[1][0][row]), w * (nj + xch[1][1][row]),
+                      w * (dn + xch[1][2][row]), __int_as_float(eq_k + ep[0] + ep[1]));
+      // q_x = P_x' (q_k o U_sibling): exponents of q_k and of the sibling;
+      // part B adds the rescale of q_x
+      for (int x = 0; x < 2; ++x)
+        if (xs[x].internal)
+          a.pre_escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c] = eq_k + ep[1 - x];
+    }
+  }
+  TCB_EPILOGUE(512)
+}
+
+// ---------------------------------------------------------------------------
+// Pre-order level, part B: q_x = a_x P_x for the internal children, in
+// place of a_x, rescaled.  blockIdx.y = 2 (level node) + child.
+// ---------------------------------------------------------------------------
+template <typename T>  // float only
+__global__ void __launch_bounds__(kTcThreads) pre_tcb_b_kernel(LevelArgs<T> a) {
+  pdl_wait_and_release();
+  const int4 d = a.level_desc[blockIdx.y >> 1];
+  const int xb = (blockIdx.y & 1) ? d.z : d.y;
+  if (xb < a.n_tips) return;  // a tip child has no q (the whole block leaves)
+  TCB_PROLOGUE(128)
+  __shared__ float xch[2][kTcRows];
+  const int R = a.n_cat, C = a.n_patterns;
+  const TcChild x = tc_child(a.n_tips, xb, false);
+  const int c0 = blockIdx.x * kTcRows, c = c0 + row;
+  const bool valid = c < C;
+  const int r = blockIdx.z, estr = a.escale_stride;
+  const size_t xslot = (size_t)(xb - a.n_tips);
+  const size_t stride = (size_t)R * kTcbSP;
+  float* arow = a.pre + (xslot * C * R + r) * kTcbSP;  // a_x rows in, q_x rows out
+  bool ok = true;
+  // rounds kb: q_x (+)= a_x[:, kb] P'_x[:, kb]' (both buffers fresh: no wait)
+  for (int kb = 0; kb < kTcbNB && ok; ++kb)
+    ok = tcb_round(A, B, bars, ph, kb, tcb_unit(a, xb, r) + tcb_block(2, 0, kb), true, kb, a, x,
+                   arow, stride, kb, c0, tmem, kb > 0);
+  for (int b = 0; b < 2 && ok; ++b) ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err);
+  if (ok) {
+    float q[64];
+    float m = 0.f;
+    tc::ld32(trow + 64 * h, *reinterpret_cast<float(*)[32]>(q));
+    tc::ld32(trow + 64 * h + 32, *reinterpret_cast<float(*)[32]>(q + 32));
+#pragma unroll
+    for (int i = 0; i < 64; ++i) m = fmaxf(m, fabsf(q[i]));
+    xch[h][row] = m;
+    __syncthreads();
+    m = fmaxf(m, xch[1 - h][row]);
+    int e = 0;
+    if (valid) {
+      if (!isfinite(m)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      else if (m > 0.f) (void)frexpf(m, &e);
+      e = max(e, -126);
+    }
+    const float f = ldexpf(1.f, -e);
+    float* st = reinterpret_cast<float*>(base);  // A is free: every MMA is done
+#pragma unroll
+    for (int i = 0; i < 64; i += 4)
+      *reinterpret_cast<float4*>(st + row * kTcbLd + 64 * h + i) =
+          make_float4(q[i] * f, q[i + 1] * f, q[i + 2] * f, q[i + 3] * f);
+    if (valid && h == 0) a.pre_escale[(xslot * R + r) * estr + c] += e;
+    __syncthreads();
+    tcb_store_rows(arow, stride, c0, C, st);
+  }
+  TCB_EPILOGUE(128)
+}
+
+#undef TCB_PROLOGUE
+#undef TCB_EPILOGUE
+
+inline cudaError_t launch_tcb(const LevelArgs<float>& a, bool post, cudaStream_t st) {
+  if (post) {
+    dim3 grid(a.n_tiles, a.n_level, a.n_cat);
+    cudaError_t e = launch_pdl(post_tcb_kernel<float>, grid, kTcThreads, kTcbSmem, st, a);
+    if (e == cudaSuccess && a.root_level)
+      e = launch_pdl(root_tcb_kernel<float>, dim3(a.n_tiles), kTcRows, 0, st, a);
+    return e;
+  }
+  dim3 ga(a.n_tiles, a.n_level, a.n_cat);
+  cudaError_t e = launch_pdl(pre_tcb_a_kernel<float>, ga, kTcThreads, kTcbSmem, st, a);
+  if (e != cudaSuccess) return e;
+  dim3 gb(a.n_tiles, 2 * a.n_level, a.n_cat);
+  return launch_pdl(pre_tcb_b_kernel<float>, gb, kTcThreads, kTcbSmem, st, a);
+}
+
+inline cudaError_t launch_pmat_tcb(const PmatArgs& a, cudaStream_t st) {
+  cudaError_t e = launch_pmat_big<kTcbSP>(a, st);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (long long)a.n_branches * a.n_cat * 3 * kTcbNB * kTcbNB;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  tcb_tiles_kernel<float><<<(unsigned)blocks, 64, 0, st>>>(static_cast<const float*>(a.P),
+                                                     static_cast<const float*>(a.dP),
+                                                     static_cast<unsigned char*>(a.tiles));
+  return cudaGetLastError();
+}
+
+inline cudaError_t prepare_tcb() {
+  cudaError_t e = cudaFuncSetAttribute(post_tcb_kernel<float>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kTcbSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pre_tcb_a_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcbSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pre_tcb_b_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcbSmem);
+  return e;
+}
+
+}  // namespace phylo

@@ -43,6 +43,7 @@ struct Layout {
   Region tip_states, tip_partials, tip_has;
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
   Region vsplit;  // tensor-core path: eigenvectors as double-float tables
+  Region tc_tiles;  // 65..128 states, FP32: pre-split matrix blocks
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
   Region gpart, lpart, out;  // out = [logL, grad...] followed by the flag word
   Region chain_a, chain_b, chain_out, chain_idx;  // chain-rule epilogue staging
@@ -96,6 +97,10 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.pre_desc, n_int * sizeof(int4));
   ok &= add_region(L, L.P, mat);
   ok &= add_region(L, L.dP, tc || p4 ? 0 : mat);  // else the P region holds dP
+  if (uses_tc_big(L.SP, prec == PHYLO_FP64)) {
+    if (!mul_ok(n_br * R, kTcbUnitBytes, &tmp)) return "size overflow";
+    ok &= add_region(L, L.tc_tiles, tmp);
+  }
   ok &= add_region(L, L.post, part);
   ok &= add_region(L, L.pre, part);
   if (C > (1 << 30)) return "n_patterns too large";
@@ -103,7 +108,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   if (!mul_ok(n_int * planes, (size_t)round_up(C, 4) * sizeof(int), &tmp))
     return "size overflow";
   ok &= add_region(L, L.escale, tmp);
-  if (tc) {
+  if (uses_tc_terms(L.SP, prec == PHYLO_FP64)) {
     ok &= add_region(L, L.pre_escale, tmp);
     if (!mul_ok(n_int * C, (size_t)R * 16, &tmp)) return "size overflow";
     ok &= add_region(L, L.rterm, tmp);
@@ -274,6 +279,7 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.lpart = ctx->dev<double>(ctx->L.lpart);
   a.n_tiles = ctx->L.n_tiles;
   a.err = reinterpret_cast<int*>(ctx->dev<double>(ctx->L.out) + 2 * ctx->N - 1);
+  a.tc_tiles = ctx->L.tc_tiles.bytes ? ctx->dev<unsigned char>(ctx->L.tc_tiles) : nullptr;
   return a;
 }
 
@@ -308,6 +314,7 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     pa.n_cat = ctx->R;
     pa.P = ctx->dev<T>(ctx->L.P);
     pa.dP = ctx->dev<T>(ctx->L.dP);
+    pa.tiles = ctx->L.tc_tiles.bytes ? ctx->dev<void>(ctx->L.tc_tiles) : nullptr;
     pa.err = flag_word(ctx);
     return launch_pmat<T>(pa, ctx->L.SP, st);
   }
@@ -1263,8 +1270,12 @@ int phylo_launches_per_evaluation(const phylo_ctx* ctx) {
   if (!ctx || !ctx->have_tree) return 0;
   int n = 2;  // pmat + final reduction
   if (ctx->C > 0) {
+    const bool fp64 = ctx->precision == PHYLO_FP64;
     n += (int)(ctx->post_off.size() - 1) + (int)(ctx->pre_off.size() - 1);
-    if (uses_tensor_cores(ctx->L.SP, ctx->precision == PHYLO_FP64)) ++n;  // Eq. 8 ratios
+    if (uses_tc_terms(ctx->L.SP, fp64)) ++n;  // Eq. 8 ratios
+    // 65..128 states on the tensor cores: two kernels per pre-order level,
+    // Eq. 3 at the root, and the operand split after the matrix build
+    if (uses_tc_big(ctx->L.SP, fp64)) n += (int)(ctx->pre_off.size() - 1) + 2;
   }
   return n;
 }
@@ -1274,6 +1285,10 @@ int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
   if (!ctx || !n_post_levels || !n_pre_levels) return PHYLO_EINVAL;
   *n_post_levels = ctx->have_tree ? (int)ctx->post_off.size() - 1 : 0;
   *n_pre_levels = ctx->have_tree ? (int)ctx->pre_off.size() - 1 : 0;
+  if (uses_tc_big(ctx->L.SP, ctx->precision == PHYLO_FP64)) {  // see launches_per_evaluation
+    *n_post_levels += *n_post_levels > 0;
+    *n_pre_levels *= 2;
+  }
   return PHYLO_OK;
 }
 

@@ -84,6 +84,18 @@ constexpr int kTcTilePatterns = 128;
 // P' as three-term BF16 splits (kernels_tc64.cuh gives the layout).
 constexpr size_t kTcUnitBytes = 73728;
 
+// FP32 with 65..128 states runs on the tensor cores too (kernels_tcb.cuh):
+// 128-pattern tiles, per-category exponents, and the matrices pre-split into
+// 64 x 64 BF16 operand blocks (kind P, dP, P' x 2 x 2 blocks of 24 KB per
+// (branch, category)) beside the FP32 P and dP of the matrix kernel.
+inline bool uses_tc_big(int SP, bool fp64) { return SP == 128 && !fp64; }
+constexpr size_t kTcbUnitBytes = 3 * 2 * 2 * (3 * 64 * 128);
+// Paths with per-category exponents and Eq. 8 terms combined by the ratio
+// kernel (both tensor-core paths).
+inline bool uses_tc_terms(int SP, bool fp64) {
+  return uses_tensor_cores(SP, fp64) || uses_tc_big(SP, fp64);
+}
+
 // The eigenvectors as double-float pairs for the tensor-core path's matrix
 // kernel: out = [V' hi][V' lo][Vinv hi][Vinv lo] (each 64 x 64 floats, V'
 // the transpose of V, zero outside S x S) then [pi hi][pi lo] (64 each).
@@ -125,13 +137,13 @@ inline bool uses_eigen_split(int SP, bool fp64) { return !fp64; }
 // Exponent planes per node: R on the tensor-core path, else 1 (one
 // exponent per (node, pattern) shared by all categories).
 inline int escale_planes(int SP, int R, bool fp64) {
-  return uses_tensor_cores(SP, fp64) ? R : 1;
+  return uses_tc_terms(SP, fp64) ? R : 1;
 }
 
 // Patterns of one tile (the unit of the per-tile gradient sums).
 inline int patterns_per_tile(int SP, int R, bool fp64) {
   if (SP == 4 && !fp64) return kP4TilePatterns;
-  if (uses_tensor_cores(SP, fp64)) return kTcTilePatterns;
+  if (uses_tc_terms(SP, fp64)) return kTcTilePatterns;
   if (SP <= 20) return kSmallThreads / lanes_per_pattern(R);
   if (SP >= 128) return fp64 ? kBigPatternsF64 : kBigPatternsF32;
   return fp64 ? kWidePatternsF64 : kWidePatternsF32;
@@ -188,6 +200,8 @@ struct LevelArgs {
   double* lpart;               // [n_tiles] per-tile log-likelihood sums
   int n_tiles;
   int* err;                    // numeric flags
+  const unsigned char* tc_tiles;  // 65..128 states, FP32: the pre-split matrix
+                                  // blocks [2N-2][R][kTcbUnitBytes] (else null)
 };
 
 struct PmatArgs {
@@ -201,6 +215,7 @@ struct PmatArgs {
   int n_branches, n_states, n_cat;
   void* P;               // [n_branches][R][SP][SP] of T
   void* dP;
+  void* tiles;           // 65..128 states, FP32: pre-split matrix blocks (else null)
   int* err;
 };
 

@@ -140,6 +140,22 @@ __device__ __forceinline__ void mma_split_bf16x3(uint32_t d_tmem, const uint32_t
                (p | kk) ? 1 : 0);
 }
 
+// The same six products accumulated onto D (accumulate = true) or
+// overwriting it: one K-block of a K-tiled contraction.
+template <int N>
+__device__ __forceinline__ void mma_split_bf16x3_acc(uint32_t d_tmem, const uint32_t (&a)[3],
+                                                     const uint32_t (&b)[3], bool accumulate) {
+  constexpr uint32_t id = idesc_bf16(128, N);
+  constexpr int pa[6] = {0, 0, 1, 0, 1, 2};
+  constexpr int pb[6] = {0, 1, 0, 2, 1, 0};
+#pragma unroll
+  for (int p = 0; p < 6; ++p)
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+      mma_bf16(d_tmem, desc(a[pa[p]] + kk * 32), desc(b[pb[p]] + kk * 32), id,
+               (accumulate || p || kk) ? 1 : 0);
+}
+
 // Split 8 FP32 values into three BF16 terms x = t0 + t1 + t2 (each term
 // the round-to-nearest BF16 of the remainder so far; the remainders are
 // exact in FP32) and store the three 16-byte chunks of row `row`, chunk j.
