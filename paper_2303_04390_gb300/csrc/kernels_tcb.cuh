@@ -42,6 +42,8 @@ static_assert(kTcbUnitBytes == 3 * kTcbNB * kTcbNB * kTcbBlock, "tile block size
 constexpr size_t kTcbSmem = 1024 + 2 * (size_t)kOp128 + 4 * (size_t)kTcbBlock;
 constexpr int kTcbLd = kTcbSP + 4;           // output staging row stride (floats)
 static_assert((size_t)kTcRows * kTcbLd * 4 <= 2 * (size_t)kOp128, "staging fits in A");
+static_assert(2 * (size_t)kTcRows * kTcbLd * 4 <= 2 * (size_t)kOp128 + 4 * (size_t)kTcbBlock,
+              "two staging buffers fit in A and B");
 
 // Offset of block (kind, jn, jk) in a (branch, category) unit of tiles:
 // kind 0 = P, 1 = dP, 2 = P' (its rows are the columns of P); block row n,
@@ -93,31 +95,47 @@ __device__ __forceinline__ const unsigned char* tcb_unit(const LevelArgs<float>&
   return a.tc_tiles + ((size_t)b * a.n_cat + r) * kTcbUnitBytes;
 }
 
-// Fill the A operand with K-block kb (states 64 kb .. 64 kb + 63) of a
-// child's rows: its partials, or for a compact tip its one-hot rows (all
-// ones up to S for a gap; zero rows past the last pattern).
-__device__ __forceinline__ void tcb_fill_a(unsigned char* A, const LevelArgs<float>& a,
-                                           const TcChild& x, const float* src, size_t stride,
-                                           int kb, int c0) {
-  const int C = a.n_patterns, S = a.n_states;
+// The loads of one A fill (K-block kb, states 64 kb .. 64 kb + 63, of a
+// child's rows), issued a round ahead of their use: the partial rows, or for
+// a compact tip its states (the fill then writes one-hot rows, all ones up
+// to S for a gap, zero rows past the last pattern).
+struct TcbFill {
+  float4 v[8];
+  int y[4];
+};
+
+__device__ __forceinline__ void tcb_load_fill(TcbFill& f, const LevelArgs<float>& a,
+                                              const TcChild& x, const float* src, size_t stride,
+                                              int kb, int c0) {
+  const int C = a.n_patterns;
   if (!x.compact) {
-    float4 v[8];
-    coop_load(v, src + 64 * kb, stride, c0, C);
-    coop_put(A, v);
+    coop_load(f.v, src + 64 * kb, stride, c0, C);
+    return;
+  }
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int c = c0 + coop_row(it);
+    f.y[it] = c < C ? (int)a.tip_states[(size_t)x.b * a.state_stride + c] : -1;
+  }
+}
+
+__device__ __forceinline__ void tcb_put_fill(unsigned char* A, const TcbFill& f,
+                                             const TcChild& x, int kb, int S) {
+  if (!x.compact) {
+    coop_put(A, f.v);
     return;
   }
   const int j = threadIdx.x & 7;
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
-    const int m = coop_row(it), c = c0 + m;
-    const int y = c < C ? (int)a.tip_states[(size_t)x.b * a.state_stride + c] : -1;
+    const int y = f.y[it];
     float v8[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int kk = 64 * kb + 8 * j + i;
       v8[i] = y < 0 ? 0.f : y < S ? (kk == y ? 1.f : 0.f) : (kk < S ? 1.f : 0.f);
     }
-    tc::put_split3(A, A + kTerm128, A + 2 * kTerm128, m, j, v8);
+    tc::put_split3(A, A + kTerm128, A + 2 * kTerm128, coop_row(it), j, v8);
   }
 }
 
@@ -154,32 +172,45 @@ __device__ __forceinline__ void tcb_store_rows(float* __restrict__ base, size_t 
 }
 
 // Bookkeeping of the asynchronous phases a CTA has issued and waited on,
-// so that a timeout can drain what is still in flight.
+// so that a timeout can drain what is still in flight.  Barriers: 0, 1 =
+// bulk copies into B buffer 0, 1; 2, 3 = MMA commits of rounds using B
+// buffer 0, 1.  Scalars (not arrays), so that they stay in registers.
 struct TcbPhases {
-  uint32_t issued[4], waited[4];  // bars: tma 0, tma 1, mma 0, mma 1
+  uint32_t i0 = 0, i1 = 0, i2 = 0, i3 = 0;  // issued
+  uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;  // waited
+  __device__ uint32_t waited(int k) const { return k == 0 ? w0 : k == 1 ? w1 : k == 2 ? w2 : w3; }
+  __device__ void wait_done(int k) {
+    w0 += k == 0; w1 += k == 1; w2 += k == 2; w3 += k == 3;
+  }
+  __device__ void issue(int k) {
+    i0 += k == 0; i1 += k == 1; i2 += k == 2; i3 += k == 3;
+  }
 };
 
-__device__ __forceinline__ bool tcb_wait(uint64_t* bar, TcbPhases& ph, int i, int* err) {
-  const bool mine = mbar_wait(bar, ph.waited[i] & 1);
+__device__ __forceinline__ bool tcb_wait(uint64_t* bars, TcbPhases& ph, int k, int* err) {
+  const bool mine = mbar_wait(&bars[k], ph.waited(k) & 1);
   const bool ok = __syncthreads_and(mine);
-  if (ok) ++ph.waited[i];
+  if (ok) ph.wait_done(k);
   else if (threadIdx.x == 0) atomicOr(err, ERR_TIMEOUT);
   tc::fence_after();
   return ok;
 }
 
 __device__ __forceinline__ void tcb_drain(uint64_t* bars, const TcbPhases& ph) {
-  if (threadIdx.x == 0)
-    for (int i = 0; i < 4; ++i)
-      for (uint32_t p = ph.waited[i]; p < ph.issued[i]; ++p) (void)mbar_wait(&bars[i], p & 1);
+  if (threadIdx.x != 0) return;
+  const uint32_t iss[4] = {ph.i0, ph.i1, ph.i2, ph.i3};
+  const uint32_t wai[4] = {ph.w0, ph.w1, ph.w2, ph.w3};
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    for (uint32_t p = wai[k]; p < iss[k]; ++p) (void)mbar_wait(&bars[k], p & 1);
 }
 
 // Common prologue: barriers, TMEM, the block's row and half.
 #define TCB_PROLOGUE(COLS)                                                   \
   extern __shared__ unsigned char smraw[];                                   \
   unsigned char* base = align1024(smraw);                                    \
-  unsigned char* A[2] = {base, base + kOp128};                               \
-  unsigned char* B[2] = {base + 2 * kOp128, base + 2 * kOp128 + 2 * kTcbBlock}; \
+  unsigned char* const A0 = base;                                           \
+  unsigned char* const B0 = base + 2 * kOp128;                               \
   __shared__ uint64_t bars[4]; /* tma 0, tma 1, mma 0, mma 1 */              \
   __shared__ uint32_t tmem_slot;                                             \
   const int tid = threadIdx.x, warp = tid >> 5;                              \
@@ -191,7 +222,7 @@ __device__ __forceinline__ void tcb_drain(uint64_t* bars, const TcbPhases& ph) {
   tc::fence_after();                                                         \
   const uint32_t tmem = tmem_slot;                                           \
   const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);          \
-  TcbPhases ph = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+  TcbPhases ph;
 
 #define TCB_EPILOGUE(COLS)                                                   \
   tcb_drain(bars, ph);                                                       \
@@ -199,29 +230,96 @@ __device__ __forceinline__ void tcb_drain(uint64_t* bars, const TcbPhases& ph) {
   __syncthreads();                                                           \
   if (warp == 0) tc::dealloc(tmem, COLS);
 
-// One round of a contraction: copy the two B blocks at `bsrc` (blocks jn =
-// 0, 1 of one kind and K-block) into buffer b, optionally refill A buffer
-// `ab` with K-block kb of a child's rows, then (thread 0) issue the round's
-// MMAs into d_tmem once the copies have landed.
-__device__ __forceinline__ bool tcb_round(unsigned char* const (&A)[2],
-                                          unsigned char* const (&B)[2], uint64_t* bars,
-                                          TcbPhases& ph, int b, const unsigned char* bsrc,
-                                          bool fill, int ab, const LevelArgs<float>& a,
-                                          const TcChild& x, const float* src, size_t stride,
-                                          int kb, int c0, uint32_t d_tmem, bool accumulate) {
+// The rounds of a K- and N-tiled contraction.  Round i multiplies A buffer
+// ab (a K-block of a child's rows, written by fill `fill` if >= 0) by the two
+// matrix blocks at bsrc (blocks jn = 0, 1 of one kind and K-block, staged
+// in B buffer i & 1) into d_tmem.  The rounds are pipelined: while round i's
+// MMAs run, round i + 1's blocks are copied in and its A fill is written,
+// and the loads of the fill after that are in flight.  Rounds and fills come
+// from generator functions of their index (nothing indexed at run time lives
+// in local memory); fills are written in index order.
+struct TcbNext {
+  TcChild x;
+  const float* src;
+  size_t stride;
+  int kb;
+};
+
+struct TcbRound {
+  const unsigned char* bsrc;
+  int fill;  // the fill written before this round, or -1 (A buffer ab holds it)
+  int ab;
+  uint32_t d_tmem;
+  bool accumulate;
+};
+
+// A buffers at A0 + ab kOp128, B buffers at B0 + b 2 kTcbBlock.
+__device__ __forceinline__ unsigned char* tcb_a(unsigned char* A0, int ab) {
+  return A0 + (size_t)ab * kOp128;
+}
+__device__ __forceinline__ unsigned char* tcb_b(unsigned char* B0, int b) {
+  return B0 + (size_t)b * 2 * kTcbBlock;
+}
+
+__device__ __forceinline__ void tcb_issue_b(unsigned char* B0, uint64_t* bars, TcbPhases& ph,
+                                            int i, const unsigned char* bsrc) {
   if (threadIdx.x == 0) {
+    const int b = i & 1;
     mbar_expect_tx(&bars[b], 2 * kTcbBlock);
-    ++ph.issued[b];
-    bulk_g2s(B[b], bsrc, 2 * kTcbBlock, &bars[b]);
+    ph.issue(b);
+    bulk_g2s(tcb_b(B0, b), bsrc, 2 * kTcbBlock, &bars[b]);
   }
-  if (fill) tcb_fill_a(A[ab], a, x, src, stride, kb, c0);
-  tc::fence_smem_for_async();
-  if (!tcb_wait(&bars[b], ph, b, a.err)) return false;
-  if (threadIdx.x == 0) {
-    tcb_mma_round(d_tmem, A[ab], B[b], accumulate);
-    tc::commit(&bars[2 + b]);
-    ++ph.issued[2 + b];
+}
+
+// Runs n rounds; false on a timeout (ERR_TIMEOUT raised).  On success every
+// MMA has completed and the accumulators can be read.
+template <class RoundOf, class FillOf>
+__device__ __forceinline__ bool tcb_pipeline(unsigned char* A0, unsigned char* B0, uint64_t* bars,
+                                             TcbPhases& ph, int n, int n_fills, RoundOf round_of,
+                                             FillOf fill_of, const LevelArgs<float>& a, int c0) {
+  const int S = a.n_states;
+  TcbFill f;
+  if (n_fills > 0) {
+    const TcbNext q = fill_of(0);
+    tcb_load_fill(f, a, q.x, q.src, q.stride, q.kb, c0);
   }
+  TcbRound cur = round_of(0);
+  tcb_issue_b(B0, bars, ph, 0, cur.bsrc);
+  if (cur.fill >= 0) {
+    tcb_put_fill(tcb_a(A0, cur.ab), f, fill_of(cur.fill).x, fill_of(cur.fill).kb, S);
+    tc::fence_smem_for_async();
+    if (cur.fill + 1 < n_fills) {
+      const TcbNext q = fill_of(cur.fill + 1);
+      tcb_load_fill(f, a, q.x, q.src, q.stride, q.kb, c0);
+    }
+  }
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    if (!tcb_wait(bars, ph, i & 1, a.err)) return false;  // round i's blocks (and A)
+    if (threadIdx.x == 0) {
+      tcb_mma_round(cur.d_tmem, tcb_a(A0, cur.ab), tcb_b(B0, i & 1), cur.accumulate);
+      tc::commit(&bars[2 + (i & 1)]);
+      ph.issue(2 + (i & 1));
+    }
+    if (i + 1 < n) {
+      // round i - 1 done: its B buffer, and the A buffer the next fill
+      // writes, are free
+      if (i >= 1 && !tcb_wait(bars, ph, 2 + ((i - 1) & 1), a.err)) return false;
+      cur = round_of(i + 1);
+      tcb_issue_b(B0, bars, ph, i + 1, cur.bsrc);
+      if (cur.fill >= 0) {
+        const TcbNext q = fill_of(cur.fill);
+        tcb_put_fill(tcb_a(A0, cur.ab), f, q.x, q.kb, S);
+        tc::fence_smem_for_async();
+        if (cur.fill + 1 < n_fills) {
+          const TcbNext q2 = fill_of(cur.fill + 1);
+          tcb_load_fill(f, a, q2.x, q2.src, q2.stride, q2.kb, c0);
+        }
+      }
+    }
+  }
+  for (int i = n >= 2 ? n - 2 : 0; i < n; ++i)
+    if (!tcb_wait(bars, ph, 2 + (i & 1), a.err)) return false;
   return true;
 }
 
@@ -246,17 +344,22 @@ __global__ void __launch_bounds__(kTcThreads) post_tcb_kernel(LevelArgs<T> a) {
   if (valid)
     for (int x = 0; x < 2; ++x)
       if (xs[x].internal) E += a.escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c];
-  bool ok = true;
-  // rounds i = (child x, K-block kb): U_x (+)= p_x[:, kb] P_x[:, kb]'
-  for (int i = 0; i < 2 * kTcbNB && ok; ++i) {
-    const int x = i / kTcbNB, kb = i % kTcbNB, b = i & 1;
-    if (i >= 2 && !(ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err))) break;  // round i-2
-    size_t stride = 0;
-    const float* src = xs[x].compact ? nullptr : tcb_child_base(a, xs[x], r, &stride);
-    ok = tcb_round(A, B, bars, ph, b, tcb_unit(a, xs[x].b, r) + tcb_block(0, 0, kb), true, b,
-                   a, xs[x], src, stride, kb, c0, tmem + 128 * x, kb > 0);
-  }
-  for (int b = 0; b < 2 && ok; ++b) ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err);
+  const int2 xb2 = make_int2(xs[0].b, xs[1].b);
+  size_t st0 = 0, st1 = 0;
+  const float* src0 = xs[0].compact ? nullptr : tcb_child_base(a, xs[0], r, &st0);
+  const float* src1 = xs[1].compact ? nullptr : tcb_child_base(a, xs[1], r, &st1);
+  // fill i = round i = (child x, K-block kb): U_x (+)= p_x[:, kb] P_x[:, kb]'
+  const TcChild x0 = xs[0], x1 = xs[1];
+  auto fill_of = [=](int i) {
+    const int x = i / kTcbNB;
+    return TcbNext{x ? x1 : x0, x ? src1 : src0, x ? st1 : st0, i % kTcbNB};
+  };
+  auto round_of = [=, &a](int i) {
+    const int x = i / kTcbNB, kb = i % kTcbNB;
+    return TcbRound{tcb_unit(a, x ? xb2.y : xb2.x, r) + tcb_block(0, 0, kb), i, i & 1,
+                    tmem + 128u * x, kb > 0};
+  };
+  const bool ok = tcb_pipeline(A0, B0, bars, ph, 2 * kTcbNB, 2 * kTcbNB, round_of, fill_of, a, c0);
   if (ok) {
     // epilogue: p = U_i o U_j on this half row, the row max, scale, store
     float p[64];
@@ -375,69 +478,70 @@ __global__ void __launch_bounds__(kTcThreads) pre_tcb_a_kernel(LevelArgs<T> a) {
       if (xs[x].compact) gap[x] = (int)a.tip_states[(size_t)xs[x].b * a.state_stride + c] >= S;
     }
   }
-  bool ok = true;
-  // rounds i = (child x, K-block kb, kind m in {P, dP}); A refilled when the
-  // K-block changes: [U_x | V_x] (+)= p_x[:, kb] [P_x ; dP_x][:, kb]'
-  for (int i = 0; i < 4 * kTcbNB && ok; ++i) {
-    const int x = i / (2 * kTcbNB), kb = (i / 2) % kTcbNB, m = i & 1, b = i & 1;
-    if (i >= 2 && !(ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err))) break;  // round i-2
-    size_t stride = 0;
-    const float* src = xs[x].compact ? nullptr : tcb_child_base(a, xs[x], r, &stride);
-    ok = tcb_round(A, B, bars, ph, b, tcb_unit(a, xs[x].b, r) + tcb_block(m, 0, kb), m == 0,
-                   (i / 2) & 1, a, xs[x], src, stride, kb, c0, tmem + 256 * x + 128 * m, kb > 0);
+  // the rows of q_k this thread's epilogue reads, loaded before the MMAs
+  float qv[64];
+  if (!root && valid) {
+    const float4* q4 = reinterpret_cast<const float4*>(a.pre + ((kslot * C + c) * R + r) * kTcbSP +
+                                                       64 * h);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float4 t4 = q4[i];
+      qv[4 * i] = t4.x; qv[4 * i + 1] = t4.y; qv[4 * i + 2] = t4.z; qv[4 * i + 3] = t4.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 64; ++i)
+      qv[i] = root && 64 * h + i < S ? a.root_pit[64 * h + i] : 0.f;
   }
-  for (int b = 0; b < 2 && ok; ++b) ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err);
+  const int2 xb2 = make_int2(xs[0].b, xs[1].b);
+  size_t st0 = 0, st1 = 0;
+  const float* src0 = xs[0].compact ? nullptr : tcb_child_base(a, xs[0], r, &st0);
+  const float* src1 = xs[1].compact ? nullptr : tcb_child_base(a, xs[1], r, &st1);
+  // fill (child x, K-block kb) serves rounds 2 fill and 2 fill + 1
+  const TcChild x0 = xs[0], x1 = xs[1];
+  auto fill_of = [=](int fi) {
+    const int x = fi / kTcbNB;
+    return TcbNext{x ? x1 : x0, x ? src1 : src0, x ? st1 : st0, fi % kTcbNB};
+  };
+  // rounds i = (child x, K-block kb, kind m in {P, dP}):
+  // [U_x | V_x] (+)= p_x[:, kb] [P_x ; dP_x][:, kb]'
+  auto round_of = [=, &a](int i) {
+    const int x = i / (2 * kTcbNB), kb = (i / 2) % kTcbNB, m = i & 1, fi = i / 2;
+    return TcbRound{tcb_unit(a, x ? xb2.y : xb2.x, r) + tcb_block(m, 0, kb), m == 0 ? fi : -1,
+                    fi & 1, tmem + 256u * x + 128u * m, kb > 0};
+  };
+  const bool ok = tcb_pipeline(A0, B0, bars, ph, 4 * kTcbNB, 2 * kTcbNB, round_of, fill_of, a, c0);
   if (ok) {
     // epilogue: per 16 columns of this half row
     float ni = 0.f, nj = 0.f, dn = 0.f;
-    const float* qrow = a.pre + ((kslot * C + c) * R + r) * kTcbSP;
-    float* ai_out = xs[0].internal
-                        ? a.pre + (((size_t)(xs[0].b - a.n_tips) * C + c) * R + r) * kTcbSP
-                        : nullptr;
-    float* aj_out = xs[1].internal
-                        ? a.pre + (((size_t)(xs[1].b - a.n_tips) * C + c) * R + r) * kTcbSP
-                        : nullptr;
-#pragma unroll 1
+    // a_i and a_j staged for coalesced stores (A and B are free: every MMA
+    // is done)
+    float* st[2] = {reinterpret_cast<float*>(base),
+                    reinterpret_cast<float*>(base) + kTcRows * kTcbLd};
+#pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int s0 = 64 * h + 16 * q;
-      float ui[16], vi[16], uj[16], vj[16], qv[16];
+      float ui[16], vi[16], uj[16], vj[16];
       tc::ld16(trow + 0 + s0, ui);
       tc::ld16(trow + 128 + s0, vi);
       tc::ld16(trow + 256 + s0, uj);
       tc::ld16(trow + 384 + s0, vj);
-      if (root) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) qv[i] = s0 + i < S ? a.root_pit[s0 + i] : 0.f;
-      } else if (valid) {
-#pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-          const float4 t4 = *reinterpret_cast<const float4*>(qrow + s0 + i);
-          qv[i] = t4.x; qv[i + 1] = t4.y; qv[i + 2] = t4.z; qv[i + 3] = t4.w;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) qv[i] = 0.f;
-      }
       float ai[16], aj[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        ai[i] = qv[i] * uj[i];  // a_i = q o U_j
-        aj[i] = qv[i] * ui[i];  // a_j = q o U_i
+        ai[i] = qv[16 * q + i] * uj[i];  // a_i = q o U_j
+        aj[i] = qv[16 * q + i] * ui[i];  // a_j = q o U_i
         dn = fmaf(ai[i], ui[i], dn);
         // a gap's d/dt of the all-ones vector is 0
         if (!gap[0]) ni = fmaf(ai[i], vi[i], ni);
         if (!gap[1]) nj = fmaf(aj[i], vj[i], nj);
       }
-      if (valid) {
 #pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-          if (ai_out)
-            *reinterpret_cast<float4*>(ai_out + s0 + i) =
-                make_float4(ai[i], ai[i + 1], ai[i + 2], ai[i + 3]);
-          if (aj_out)
-            *reinterpret_cast<float4*>(aj_out + s0 + i) =
-                make_float4(aj[i], aj[i + 1], aj[i + 2], aj[i + 3]);
-        }
+      for (int i = 0; i < 16; i += 4) {
+        *reinterpret_cast<float4*>(st[0] + row * kTcbLd + s0 + i) =
+            make_float4(ai[i], ai[i + 1], ai[i + 2], ai[i + 3]);
+        *reinterpret_cast<float4*>(st[1] + row * kTcbLd + s0 + i) =
+            make_float4(aj[i], aj[i + 1], aj[i + 2], aj[i + 3]);
       }
     }
     xch[h][0][row] = ni;
@@ -455,6 +559,10 @@ __global__ void __launch_bounds__(kTcThreads) pre_tcb_a_kernel(LevelArgs<T> a) {
         if (xs[x].internal)
           a.pre_escale[((size_t)(xs[x].b - a.n_tips) * R + r) * estr + c] = eq_k + ep[1 - x];
     }
+    for (int x = 0; x < 2; ++x)  // (the barrier above also orders the staging)
+      if (xs[x].internal)
+        tcb_store_rows(a.pre + ((size_t)(xs[x].b - a.n_tips) * C * R + r) * kTcbSP,
+                       (size_t)R * kTcbSP, c0, C, st[x]);
   }
   TCB_EPILOGUE(512)
 }
@@ -479,12 +587,11 @@ __global__ void __launch_bounds__(kTcThreads) pre_tcb_b_kernel(LevelArgs<T> a) {
   const size_t xslot = (size_t)(xb - a.n_tips);
   const size_t stride = (size_t)R * kTcbSP;
   float* arow = a.pre + (xslot * C * R + r) * kTcbSP;  // a_x rows in, q_x rows out
-  bool ok = true;
-  // rounds kb: q_x (+)= a_x[:, kb] P'_x[:, kb]' (both buffers fresh: no wait)
-  for (int kb = 0; kb < kTcbNB && ok; ++kb)
-    ok = tcb_round(A, B, bars, ph, kb, tcb_unit(a, xb, r) + tcb_block(2, 0, kb), true, kb, a, x,
-                   arow, stride, kb, c0, tmem, kb > 0);
-  for (int b = 0; b < 2 && ok; ++b) ok = tcb_wait(&bars[2 + b], ph, 2 + b, a.err);
+  auto fill_of = [=](int kb) { return TcbNext{x, arow, stride, kb}; };
+  auto round_of = [=, &a](int kb) {  // q_x (+)= a_x[:, kb] P'_x[:, kb]'
+    return TcbRound{tcb_unit(a, xb, r) + tcb_block(2, 0, kb), kb, kb, tmem, kb > 0};
+  };
+  const bool ok = tcb_pipeline(A0, B0, bars, ph, kTcbNB, kTcbNB, round_of, fill_of, a, c0);
   if (ok) {
     float q[64];
     float m = 0.f;
