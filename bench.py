@@ -573,7 +573,7 @@ def rooflines(w, precision, phase_ms, level_counts, peaks, n_sm, workload):
                    "pre": "pre_tc_kernel + ratio_tc_kernel",
                    "reduce": "reduce_kernel"}
     if precision == "fp32" and 64 < w.n_states <= 128:
-        kernels = {"pmat": "pmat_big_df_kernel + tcb_tiles_kernel",
+        kernels = {"pmat": "pmat_big_df_kernel (writes the split operand blocks)",
                    "post": "post_tcb_kernel + root_tcb_kernel",
                    "pre": "pre_tcb_a_kernel + pre_tcb_b_kernel + ratio_tc_kernel",
                    "reduce": "reduce_kernel"}

@@ -617,11 +617,68 @@ __global__ void __launch_bounds__(256) pmat_big_df_kernel(PmatArgs a) {
       }
     }
   }
-  float* P = static_cast<float*>(a.P) + (size_t)unit * sq;
-  float* D = static_cast<float*>(a.dP) + (size_t)unit * sq;
   const int s0 = 64 * sb + ls, t0 = 64 * tb + lt;
   const float* pi_h = a.vsplit + 4 * sq;
   const float* pi_l = pi_h + SP;
+  if constexpr (SP == 128) {
+    if (a.tiles) {
+      // the tensor-core path's operand blocks instead of P and dP: entry
+      // (s, t) goes to row s % 64, column t % 64 of blocks P (sb, tb) and dP
+      // (sb, tb), and to row t % 64, column s % 64 of block P' (tb, sb); the
+      // mirror entries (t, s) of a reversible model to the transposed places
+      unsigned char* U = static_cast<unsigned char*>(a.tiles) + (size_t)unit * kTcbUnitBytes;
+      float p[4][4], d[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int s = s0 + i, t = t0 + j;
+          DF kp = accP[i][j], kd = accD[i][j];
+          if (rev) {
+            const DF pt = {pi_h[t], pi_l[t]};
+            kp = df_mul(kp, pt);
+            kd = df_mul(kd, pt);
+          }
+          p[i][j] = df_round(kp, s == t && s < S);
+          d[i][j] = df_round(kd, false);
+        }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        put_split3_4(U + tcb_block(0, sb, tb), kTerm64, ls + i, lt,
+                     make_float4(p[i][0], p[i][1], p[i][2], p[i][3]));
+        put_split3_4(U + tcb_block(1, sb, tb), kTerm64, ls + i, lt,
+                     make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        put_split3_4(U + tcb_block(2, tb, sb), kTerm64, lt + j, ls,
+                     make_float4(p[0][j], p[1][j], p[2][j], p[3][j]));
+      if (rev && sb != tb) {  // mirror: P[t][s] = delta + K_st pi_s
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const DF ps = {pi_h[s0 + i], pi_l[s0 + i]};
+            p[i][j] = df_round(df_mul(accP[i][j], ps), false);  // = P[t][s]
+            d[i][j] = df_round(df_mul(accD[i][j], ps), false);
+          }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          put_split3_4(U + tcb_block(0, tb, sb), kTerm64, lt + j, ls,
+                       make_float4(p[0][j], p[1][j], p[2][j], p[3][j]));
+          put_split3_4(U + tcb_block(1, tb, sb), kTerm64, lt + j, ls,
+                       make_float4(d[0][j], d[1][j], d[2][j], d[3][j]));
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          put_split3_4(U + tcb_block(2, sb, tb), kTerm64, ls + i, lt,
+                       make_float4(p[i][0], p[i][1], p[i][2], p[i][3]));
+      }
+      return;
+    }
+  }
+  float* P = static_cast<float*>(a.P) + (size_t)unit * sq;
+  float* D = static_cast<float*>(a.dP) + (size_t)unit * sq;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int s = s0 + i;

@@ -16,8 +16,8 @@
 // Each group is the BF16 x3 split of tc.cuh (six products per FP32
 // product), so results carry FP32 accuracy.  Partial tiles are split into
 // their three BF16 terms in shared memory (the A operand, one 64-column
-// K-block at a time); the matrix blocks come pre-split from
-// tcb_tiles_kernel and are bulk-copied (cp.async.bulk).  A and B buffers
+// K-block at a time); the matrix kernel writes the matrix blocks pre-split
+// (tcb_block) and they are bulk-copied (cp.async.bulk).  A and B buffers
 // are double-buffered, so one round's loads and splits overlap the previous
 // round's MMAs.  A compact tip child enters the MMA as its one-hot (or, for
 // a gap, all-ones) rows, so every child takes the same path.
@@ -44,38 +44,6 @@ constexpr int kTcbLd = kTcbSP + 4;           // output staging row stride (float
 static_assert((size_t)kTcRows * kTcbLd * 4 <= 2 * (size_t)kOp128, "staging fits in A");
 static_assert(2 * (size_t)kTcRows * kTcbLd * 4 <= 2 * (size_t)kOp128 + 4 * (size_t)kTcbBlock,
               "two staging buffers fit in A and B");
-
-// Offset of block (kind, jn, jk) in a (branch, category) unit of tiles:
-// kind 0 = P, 1 = dP, 2 = P' (its rows are the columns of P); block row n,
-// column k holds M[64 jn + n][64 jk + k].  The blocks of one K-block jk are
-// adjacent (jn fastest), so one bulk copy stages a round's B operand.
-__host__ __device__ constexpr size_t tcb_block(int kind, int jn, int jk) {
-  return (((size_t)kind * kTcbNB + jk) * kTcbNB + jn) * kTcbBlock;
-}
-
-// Pre-split matrix blocks of every (branch, category) from the FP32 P and dP
-// of the matrix kernel: one CTA per block, thread n writes block row n.
-template <typename T>  // float only (a template: the header is in two units)
-__global__ void __launch_bounds__(64) tcb_tiles_kernel(const T* __restrict__ P,
-                                                       const T* __restrict__ D,
-                                                       unsigned char* __restrict__ tiles) {
-  constexpr int NBLK = 3 * kTcbNB * kTcbNB;
-  const int unit = blockIdx.x / NBLK, blk = blockIdx.x % NBLK;
-  const int kind = blk / (kTcbNB * kTcbNB), jn = (blk / kTcbNB) % kTcbNB, jk = blk % kTcbNB;
-  const T* M = (kind == 1 ? D : P) + (size_t)unit * kTcbSP * kTcbSP;
-  unsigned char* out = tiles + (size_t)unit * kTcbUnitBytes + tcb_block(kind, jn, jk);
-  const int n = threadIdx.x, nn = 64 * jn + n;
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    float x[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int kk = 64 * jk + 8 * j + i;
-      x[i] = kind == 2 ? M[(size_t)kk * kTcbSP + nn] : M[(size_t)nn * kTcbSP + kk];
-    }
-    tc::put_split3(out, out + kTerm64, out + 2 * kTerm64, n, j, x);
-  }
-}
 
 // First row (pattern 0, category r) of a non-compact child's partials on
 // this path and the row stride, in floats.
@@ -640,15 +608,7 @@ inline cudaError_t launch_tcb(const LevelArgs<float>& a, bool post, cudaStream_t
 }
 
 inline cudaError_t launch_pmat_tcb(const PmatArgs& a, cudaStream_t st) {
-  cudaError_t e = launch_pmat_big<kTcbSP>(a, st);
-  if (e != cudaSuccess) return e;
-  const long long blocks = (long long)a.n_branches * a.n_cat * 3 * kTcbNB * kTcbNB;
-  if (blocks <= 0) return cudaSuccess;
-  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  tcb_tiles_kernel<float><<<(unsigned)blocks, 64, 0, st>>>(static_cast<const float*>(a.P),
-                                                     static_cast<const float*>(a.dP),
-                                                     static_cast<unsigned char*>(a.tiles));
-  return cudaGetLastError();
+  return launch_pmat_big<kTcbSP>(a, st);  // (writes the operand blocks: a.tiles is set)
 }
 
 inline cudaError_t prepare_tcb() {

@@ -98,6 +98,9 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   ok &= add_region(L, L.P, mat);
   ok &= add_region(L, L.dP, tc || p4 ? 0 : mat);  // else the P region holds dP
   if (uses_tc_big(L.SP, prec == PHYLO_FP64)) {
+    // the matrix kernel writes the operand blocks instead of P and dP
+    L.P.bytes = L.dP.bytes = 0;
+    L.total = L.P.off;
     if (!mul_ok(n_br * R, kTcbUnitBytes, &tmp)) return "size overflow";
     ok &= add_region(L, L.tc_tiles, tmp);
   }
@@ -1273,9 +1276,9 @@ int phylo_launches_per_evaluation(const phylo_ctx* ctx) {
     const bool fp64 = ctx->precision == PHYLO_FP64;
     n += (int)(ctx->post_off.size() - 1) + (int)(ctx->pre_off.size() - 1);
     if (uses_tc_terms(ctx->L.SP, fp64)) ++n;  // Eq. 8 ratios
-    // 65..128 states on the tensor cores: two kernels per pre-order level,
-    // Eq. 3 at the root, and the operand split after the matrix build
-    if (uses_tc_big(ctx->L.SP, fp64)) n += (int)(ctx->pre_off.size() - 1) + 2;
+    // 65..128 states on the tensor cores: two kernels per pre-order level
+    // and Eq. 3 at the root
+    if (uses_tc_big(ctx->L.SP, fp64)) n += (int)(ctx->pre_off.size() - 1) + 1;
   }
   return n;
 }

@@ -85,11 +85,19 @@ constexpr int kTcTilePatterns = 128;
 constexpr size_t kTcUnitBytes = 73728;
 
 // FP32 with 65..128 states runs on the tensor cores too (kernels_tcb.cuh):
-// 128-pattern tiles, per-category exponents, and the matrices pre-split into
-// 64 x 64 BF16 operand blocks (kind P, dP, P' x 2 x 2 blocks of 24 KB per
-// (branch, category)) beside the FP32 P and dP of the matrix kernel.
+// 128-pattern tiles, per-category exponents, and the matrices written by
+// the matrix kernel directly as 64 x 64 BF16 operand blocks (kind P, dP, P'
+// x 2 x 2 blocks of 24 KB per (branch, category)).
 inline bool uses_tc_big(int SP, bool fp64) { return SP == 128 && !fp64; }
 constexpr size_t kTcbUnitBytes = 3 * 2 * 2 * (3 * 64 * 128);
+// Offset of block (kind, jn, jk) in a (branch, category) unit: kind 0 = P,
+// 1 = dP, 2 = P' (its rows are the columns of P); block row n, column k
+// holds M[64 jn + n][64 jk + k] as three BF16 terms of 8 KB each, in the
+// K-major 128-byte-swizzle layout of tc.cuh.  The blocks of one K-block jk
+// are adjacent (jn fastest), so one bulk copy stages a contraction round.
+__host__ __device__ constexpr size_t tcb_block(int kind, int jn, int jk) {
+  return (((size_t)kind * 2 + jk) * 2 + jn) * (3 * 64 * 128);
+}
 // Paths with per-category exponents and Eq. 8 terms combined by the ratio
 // kernel (both tensor-core paths).
 inline bool uses_tc_terms(int SP, bool fp64) {
@@ -215,7 +223,8 @@ struct PmatArgs {
   int n_branches, n_states, n_cat;
   void* P;               // [n_branches][R][SP][SP] of T
   void* dP;
-  void* tiles;           // 65..128 states, FP32: pre-split matrix blocks (else null)
+  void* tiles;           // 65..128 states, FP32: the matrices written as pre-split
+                         // operand blocks instead of P and dP (else null)
   int* err;
 };
 
