@@ -28,6 +28,7 @@ _MAKERS = {
     "codon-128": synth.workload_codon_128,
     "hky-1024": synth.workload_hky_1024,
     "aa-256": synth.workload_aa_256,
+    "mmm-122": synth.workload_mmm_122,
 }
 _PHASES = ("pmat", "post", "pre", "reduce")
 
