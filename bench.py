@@ -86,14 +86,21 @@ def algorithmic_bytes(w, precision):
     }
 
 
-def algorithmic_flops(w):
+def algorithmic_flops(w, precision="fp32"):
     """Dense contractions the method needs per evaluation (2 S^2 flops per
-    matrix-vector product of one pattern and category): a tip child's
-    product is a column lookup, so only internal non-root nodes count --
-    post-order P p once (by the parent), pre-order P p, dP p and P' a."""
+    matrix-vector product of one pattern and category).  A tip child's
+    P p is a column lookup, so in the form of Eq. 8 with dP p only internal
+    non-root nodes count: post-order P p once (by the parent), pre-order
+    P p, dP p and P' a.  The tensor-core form for 21..64 states (FP32)
+    stores U = P p in the post-order pass and writes Eq. 8's numerator
+    through dP = gamma Q P, so its pre-order pass needs P' a of every
+    internal child and Q' a of every child, tips included."""
     N, C, S, R = w.n_tips, w.n_patterns, w.n_states, w.n_categories
-    unit = 2 * S * S * R * C * (N - 2)
-    return {"pmat": 0, "post": unit, "pre": 3 * unit, "reduce": 0}
+    node = 2 * S * S * R * C
+    if precision == "fp32" and 20 < S <= 64:
+        return {"pmat": 0, "post": node * (N - 2),
+                "pre": node * ((N - 2) + (2 * N - 2)), "reduce": 0}
+    return {"pmat": 0, "post": node * (N - 2), "pre": 3 * node * (N - 2), "reduce": 0}
 
 
 # ---------------------------------------------------------------------------
@@ -563,14 +570,14 @@ def rooflines(w, precision, phase_ms, level_counts, peaks, n_sm, workload):
     peak_kind = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
     by = algorithmic_bytes(w, precision)
-    fl = algorithmic_flops(w)
+    fl = algorithmic_flops(w, precision)
     names = ["pmat", "post", "pre", "reduce"]
     kernels = {"pmat": "pmat_kernel", "post": "post-order level kernel",
                "pre": "pre-order level kernel (fused gradient)",
                "reduce": "reduce_kernel"}
     if precision == "fp32" and 20 < w.n_states <= 64:
-        kernels = {"pmat": "pmat_tc_kernel", "post": "post_tc_pipe_kernel",
-                   "pre": "pre_tc_kernel + ratio_tc_kernel",
+        kernels = {"pmat": "pmat_tc_kernel", "post": "post_u_kernel + root_u_kernel",
+                   "pre": "pre_u_kernel + ratio_tc_kernel",
                    "reduce": "reduce_kernel"}
     if precision == "fp32" and 64 < w.n_states <= 128:
         kernels = {"pmat": "pmat_big_df_kernel (writes the split operand blocks)",

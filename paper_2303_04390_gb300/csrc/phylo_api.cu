@@ -44,6 +44,9 @@ struct Layout {
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
   Region vsplit;  // tensor-core path: eigenvectors as double-float tables
   Region tc_tiles;  // 65..128 states, FP32: pre-split matrix blocks
+  Region qt;        // 21..64 states, FP32: Q' as a tensor-core operand
+  Region tip_desc;  // 21..64 states, FP32, with tip partials: descriptors of
+                    // the tips whose U = P p the first post-order launch forms
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
   Region gpart, lpart, out;  // out = [logL, grad...] followed by the flag word
   Region chain_a, chain_b, chain_out, chain_idx;  // chain-rule epilogue staging
@@ -104,8 +107,17 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
     if (!mul_ok(n_br * R, kTcbUnitBytes, &tmp)) return "size overflow";
     ok &= add_region(L, L.tc_tiles, tmp);
   }
-  ok &= add_region(L, L.post, part);
+  if (tc && (flags & PHYLO_FLAG_TIP_PARTIALS)) {
+    // the post region holds U = P p of every internal node, then of every tip
+    if (!mul_ok(n_int + N, per_node, &tmp) || !mul_ok(tmp, L.elem, &tmp2))
+      return "size overflow";
+    ok &= add_region(L, L.post, tmp2);
+    ok &= add_region(L, L.tip_desc, (size_t)N * sizeof(int4));
+  } else {
+    ok &= add_region(L, L.post, part);
+  }
   ok &= add_region(L, L.pre, part);
+  if (tc) ok &= add_region(L, L.qt, kTcQtBytes);
   if (C > (1 << 30)) return "n_patterns too large";
   const int planes = escale_planes(L.SP, R, prec == PHYLO_FP64);
   if (!mul_ok(n_int * planes, (size_t)round_up(C, 4) * sizeof(int), &tmp))
@@ -283,6 +295,9 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.n_tiles = ctx->L.n_tiles;
   a.err = reinterpret_cast<int*>(ctx->dev<double>(ctx->L.out) + 2 * ctx->N - 1);
   a.tc_tiles = ctx->L.tc_tiles.bytes ? ctx->dev<unsigned char>(ctx->L.tc_tiles) : nullptr;
+  a.qt = ctx->L.qt.bytes ? ctx->dev<unsigned char>(ctx->L.qt) : nullptr;
+  a.rates = ctx->dev<double>(ctx->L.rates);
+  a.tip_level = 0;
   return a;
 }
 
@@ -327,6 +342,20 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     const int* nodes = ctx->dev<int>(post ? ctx->L.post_nodes : ctx->L.pre_nodes);
     const int4* desc = ctx->dev<int4>(post ? ctx->L.post_desc : ctx->L.pre_desc);
     const std::vector<int>& off = post ? ctx->post_off : ctx->pre_off;
+    if (post && ctx->L.tip_desc.bytes && a.tip_partials) {
+      // tensor-core path: U = P p of the tips with partials, before level 1
+      NvtxRange range("phylo post-order tips with partials (Eq. 2)");
+      LevelArgs<T> at = a;
+      at.level_desc = ctx->dev<int4>(ctx->L.tip_desc);
+      at.level_nodes = nullptr;
+      at.n_level = 0;
+      for (int v : ctx->tip_has) at.n_level += v != 0;
+      at.root_level = 0;
+      at.level_cherry = 0;
+      at.tip_level = 1;
+      e = launch_post_level<T>(at, ctx->L.SP, ctx->L.RP, st);
+      if (e != cudaSuccess) return e;
+    }
     for (size_t l = 0; l + 1 < off.size(); ++l) {
       NvtxRange range(post ? "phylo post-order level (Eq. 2)"
                            : "phylo pre-order level (Eqs. 4, 8)", (int)l);
@@ -481,6 +510,16 @@ int build_schedule(phylo_ctx* ctx) {
 }
 
 int upload_descriptors(phylo_ctx* ctx) {
+  if (ctx->L.tip_desc.bytes) {
+    std::vector<int4> tips;
+    for (int x = 0; x < ctx->N; ++x)
+      if (ctx->tip_has[x]) tips.push_back(make_int4(x, -1, -1, 0));
+    if (!tips.empty()) {
+      int rc = upload(ctx, ctx->L.tip_desc, tips.data(), tips.size(), "upload tip descriptors");
+      if (rc) return rc;
+      CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    }
+  }
   for (int pass = 0; pass < 2; ++pass) {
     const std::vector<int>& nodes = pass == 0 ? ctx->post_nodes : ctx->pre_nodes;
     std::vector<int4> desc(nodes.size());
@@ -915,6 +954,12 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
     std::vector<float> split(eigen_split_floats(ctx->L.SP));
     ctx->eig_reversible = build_eigen_split(S, ctx->L.SP, V, Vinv, pi, split.data());
     if ((rc = upload(ctx, ctx->L.vsplit, split.data(), split.size(), "upload V split"))) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  }
+  if (ctx->L.qt.bytes) {
+    std::vector<unsigned char> qt(kTcQtBytes);
+    build_qt_tile(S, V, Vinv, lambda, qt.data());
+    if ((rc = upload(ctx, ctx->L.qt, qt.data(), qt.size(), "upload Q operand"))) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }
   if ((rc = upload(ctx, ctx->L.lambda, lambda, (size_t)S, "upload lambda"))) return rc;

@@ -4,6 +4,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -80,9 +81,50 @@ constexpr int kP4MatKinds = 3;
 // 128-pattern tiles and one rescale exponent per (node, category, pattern).
 inline bool uses_tensor_cores(int SP, bool fp64) { return SP == 64 && !fp64; }
 constexpr int kTcTilePatterns = 128;
-// Matrix operand tiles of one (branch, category) on that path: [P; dP] and
-// P' as three-term BF16 splits (kernels_tc64.cuh gives the layout).
-constexpr size_t kTcUnitBytes = 73728;
+// Matrix operand tiles of one (branch, category) on that path: P and P' as
+// three-term BF16 splits, then P' in FP32 (kernels_tc64.cuh gives the
+// layout); Q' as one more three-term 64 x 64 operand per model.
+constexpr size_t kTcUnitBytes = 65536;
+constexpr size_t kTcQtBytes = 3 * 64 * 128;
+
+// Round-to-nearest-even BF16 of a finite float, and back (host side).
+inline uint16_t host_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+inline float host_bf16_value(uint16_t b) {
+  const uint32_t u = (uint32_t)b << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Q' as the three-term BF16 operand of the tensor-core pre-order step (the
+// Eq. 8 numerator through dP = gamma Q P): row s holds column s of
+// Q = V diag(lambda) Vinv (FP64, rounded once to FP32), each FP32 value
+// split as x = t0 + t1 + t2 with t_i the round-to-nearest BF16 of the
+// remainder, stored in the K-major 128-byte-swizzle layout the MMAs read
+// (element (row, k) of a term at row * 128 + (((k / 8) ^ (row % 8)) * 16) +
+// (k % 8) * 2).  Rows and columns past S are zero.  out: kTcQtBytes.
+inline void build_qt_tile(int S, const double* V, const double* Vinv, const double* lambda,
+                          unsigned char* out) {
+  std::memset(out, 0, kTcQtBytes);
+  const size_t term = 64 * 128;
+  for (int s = 0; s < S; ++s)
+    for (int t = 0; t < S; ++t) {
+      double q = 0.0;  // Q[t][s]
+      for (int m = 0; m < S; ++m) q += V[t * S + m] * lambda[m] * Vinv[m * S + s];
+      float rem = (float)q;
+      const size_t off = (size_t)s * 128 + ((size_t)((t >> 3) ^ (s & 7)) << 4) + (t & 7) * 2;
+      for (int i = 0; i < 3; ++i) {
+        const uint16_t b = host_bf16(rem);
+        std::memcpy(out + i * term + off, &b, 2);
+        rem = rem - host_bf16_value(b);
+      }
+    }
+}
 
 // FP32 with 65..128 states runs on the tensor cores too (kernels_tcb.cuh):
 // 128-pattern tiles, per-category exponents, and the matrices written by
@@ -185,7 +227,9 @@ struct LevelArgs {
   const T* dP;                 // same layout: dP/dt = gamma_r Q P (null on
                                // the tensor-core and FP32 4-state paths,
                                // whose P region holds dP)
-  T* post;                     // [N-1][C][R][SP] post-order partials
+  T* post;                     // [N-1][C][R][SP] post-order partials (FP32,
+                               // 21..64 states: U = P p of every internal
+                               // node, then of every tip with partials)
   T* pre;                      // [N-1][C][R][SP] pre-order partials
   int* escale;                 // [N-1][planes][escale_stride] cumulative
                                // post-order exponents (planes: escale_planes)
@@ -210,6 +254,10 @@ struct LevelArgs {
   int* err;                    // numeric flags
   const unsigned char* tc_tiles;  // 65..128 states, FP32: the pre-split matrix
                                   // blocks [2N-2][R][kTcbUnitBytes] (else null)
+  const unsigned char* qt;     // 21..64 states, FP32: Q' operand (kTcQtBytes)
+  const double* rates;         // [R] category rates gamma_r
+  int tip_level;               // 21..64 states, FP32: the level's nodes are tips
+                               // with partials (their U = P p, before level 1)
 };
 
 struct PmatArgs {

@@ -58,7 +58,7 @@ struct NaLayout {
   int SP = 0, RP = 0, n_tiles = 0;
   NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale,
       pre_escale, rterm;
-  NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t, vsplit;
+  NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t, vsplit, qt;
   NaRegion gpart, lpart, out, pattern_wt, cat_wt, pi_t;
   size_t total = 0;
 };
@@ -98,6 +98,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
   if (tc) {
     na_add(L, L.pre_escale, eplane * R);
     na_add(L, L.rterm, n_int * (size_t)C * R * 16);
+    na_add(L, L.qt, kTcQtBytes);
   }
   na_add(L, L.tip_states, (size_t)N * tip_state_stride(C));
   na_add(L, L.pattern_w, (size_t)C * 8);
@@ -318,6 +319,11 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
     reversible = build_eigen_split(S, L.SP, V, Vinv, root_freqs, vsplit);
     NA_TRY(up(L.vsplit, vsplit, eigen_split_floats(L.SP) * sizeof(float)), "upload V split");
   }
+  static thread_local unsigned char qt[kTcQtBytes];
+  if (L.qt.bytes) {
+    build_qt_tile(S, V, Vinv, lambda, qt);
+    NA_TRY(up(L.qt, qt, kTcQtBytes), "upload Q operand");
+  }
   NA_TRY(up(L.lambda, lambda, (size_t)S * 8), "upload lambda");
   NA_TRY(up(L.pi, root_freqs, (size_t)S * 8), "upload pi");
   NA_TRY(up(L.rates, rates, (size_t)R * 8), "upload rates");
@@ -382,6 +388,9 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   a.lpart = reinterpret_cast<double*>(ws + L.lpart.off);
   a.n_tiles = L.n_tiles;
   a.err = flag;
+  a.qt = L.qt.bytes ? reinterpret_cast<const unsigned char*>(ws + L.qt.off) : nullptr;
+  a.rates = reinterpret_cast<const double*>(ws + L.rates.off);
+  a.tip_level = 0;
   const int* dpost = reinterpret_cast<const int*>(ws + L.post_nodes.off);
   const int* dpre = reinterpret_cast<const int*>(ws + L.pre_nodes.off);
   const int4* dpostd = reinterpret_cast<const int4*>(ws + L.post_desc.off);

@@ -41,7 +41,8 @@ def test_work_counts():
     """Bytes: post reads p of the internal children and writes p of the
     internal non-root nodes; pre reads q_k and p and writes q of internal
     children.  Flops: one 2 S^2 product per internal non-root node in the
-    post-order pass, three in the pre-order pass (tips are column lookups)."""
+    post-order pass, three in the pre-order pass (tips are column lookups),
+    or on the tensor-core form one per internal child and one per child."""
     sys.path.insert(0, ROOT)
     import bench
     N, S, R, C = 10, 61, 4, 100
@@ -52,9 +53,14 @@ def test_work_counts():
     assert by["post"] == 2 * (N - 2) * M + N * C + 8 * (N - 2) * C + mats + 8 * C
     assert by["pre"] == 3 * (N - 2) * M + N * C + 2 * mats + 8 * C + 8 * (2 * N - 2)
     assert bench.algorithmic_bytes(w, "fp64")["post"] > by["post"]
-    fl = bench.algorithmic_flops(w)
+    fl = bench.algorithmic_flops(w, "fp64")
     assert fl["post"] == (N - 2) * 2 * S * S * R * C
     assert fl["pre"] == 3 * fl["post"] and fl["pmat"] == 0
+    # the FP32 tensor-core form: P' a of every internal child and Q' a of
+    # every child (tips included) in the pre-order pass
+    tc = bench.algorithmic_flops(w, "fp32")
+    assert tc["post"] == fl["post"]
+    assert tc["pre"] == ((N - 2) + (2 * N - 2)) * 2 * S * S * R * C
 
 
 def test_percentiles():
