@@ -78,6 +78,13 @@ static_assert(kTcQtBytes == kOp64, "Q' operand size");
 //   pre:  a_x (128-row operand, later the W_x staging) | P_x' | Q' (64 rows
 //         each; later the q_x staging)
 constexpr size_t kPostUSmem = 1024 + kOp128 + kOp64;
+// Resident CTAs per SM the post-order kernel's registers are bounded for
+// (its shared memory admits three; bounding the registers for three spills and measured slower).
+#ifndef PHYLO_POST_U_BLOCKS
+#define PHYLO_POST_U_BLOCKS 2
+#endif
+// FP32 P' of one (branch, r): the compact-tip lookup table, staged by bulk copy.
+constexpr uint32_t kPt32Bytes = 64 * 64 * 4;
 constexpr size_t kPreUSmem = 1024 + kOp128 + 2 * kOp64;
 
 __device__ __forceinline__ float pow2i(int d) {  // 2^d for d <= 0 (0 below 2^-126)
@@ -424,48 +431,58 @@ __device__ __forceinline__ float* u_rows(const LevelArgs<float>& a, int x, int r
 }
 
 // Rows c0 + coop_row(it) of U_x for a child x, in the cooperative layout
-// (floats 8 j .. 8 j + 7, j = lane % 8), with each row's stored exponent in
-// E[it] (0 for tips) and, for a compact tip, its state in y[it] (-1
-// otherwise).  A compact tip's U_x is column y of P_x, i.e. row y of the FP32
-// P'; a gap (y = S) gives the all-ones vector over the S states.  Rows past
-// the last pattern are zero.
-__device__ __forceinline__ void coop_child_u(float4 (&v)[8], int (&E)[4], int (&y)[4],
-                                             const LevelArgs<float>& a, const TcChild& x,
-                                             int r, int c0) {
-  const int C = a.n_patterns, S = a.n_states, j = threadIdx.x & 7;
+// (floats 8 j .. 8 j + 7, j = lane % 8), in two steps.  coop_child_u_issue
+// loads the stored rows of a non-compact child with each row's exponent
+// (0 for a tip), or the states of a compact tip; coop_child_u_finish then
+// fills a compact tip's rows from its FP32 P' staged in shared memory: U_x
+// is column y of P_x, i.e. row y of P'; a gap (y = S) gives the all-ones
+// vector over the S states.  Rows past the last pattern are zero (y = -1).
+struct UFetch {
+  float4 v[8];
+  int E[4], y[4];
+};
+
+__device__ __forceinline__ void coop_child_u_issue(UFetch& f, const LevelArgs<float>& a,
+                                                   const TcChild& x, int r, int c0) {
+  const int C = a.n_patterns;
   if (!x.compact) {
-    coop_load(v, u_rows(a, x.b, r), (size_t)a.n_cat * 64, c0, C);
+    coop_load(f.v, u_rows(a, x.b, r), (size_t)a.n_cat * 64, c0, C);
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int c = c0 + coop_row(it);
-      y[it] = -1;
-      E[it] = x.internal && c < C
-                  ? a.escale[((size_t)(x.b - a.n_tips) * a.n_cat + r) * a.escale_stride + c]
-                  : 0;
+      f.y[it] = -1;
+      f.E[it] = x.internal && c < C
+                    ? a.escale[((size_t)(x.b - a.n_tips) * a.n_cat + r) * a.escale_stride + c]
+                    : 0;
     }
     return;
   }
-  const float* pt32 = reinterpret_cast<const float*>(unit_tiles(a, x.b, r) + kUnitPt32);
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const int c = c0 + coop_row(it);
-    y[it] = c < C ? (int)a.tip_states[(size_t)x.b * a.state_stride + c] : -1;
-    E[it] = 0;
+    f.y[it] = c < C ? (int)a.tip_states[(size_t)x.b * a.state_stride + c] : -1;
+    f.E[it] = 0;
   }
+}
+
+__device__ __forceinline__ void coop_child_u_finish(UFetch& f, bool compact, const float* pt32,
+                                                    int S) {
+  if (!compact) return;
+  const int j = threadIdx.x & 7;
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
-    const int yy = y[it];
+    const int yy = f.y[it];
     if (yy >= 0 && yy < S) {
       const float4* src = reinterpret_cast<const float4*>(pt32 + yy * 64 + 8 * j);
-      v[2 * it] = __ldg(src);
-      v[2 * it + 1] = __ldg(src + 1);
+      f.v[2 * it] = src[0];
+      f.v[2 * it + 1] = src[1];
     } else {
       const float g = yy < 0 ? 0.f : 1.f;  // past the last pattern, or a gap
       const int s = 8 * j;
-      v[2 * it] = make_float4(s < S ? g : 0.f, s + 1 < S ? g : 0.f, s + 2 < S ? g : 0.f,
-                              s + 3 < S ? g : 0.f);
-      v[2 * it + 1] = make_float4(s + 4 < S ? g : 0.f, s + 5 < S ? g : 0.f,
-                                  s + 6 < S ? g : 0.f, s + 7 < S ? g : 0.f);
+      f.v[2 * it] = make_float4(s < S ? g : 0.f, s + 1 < S ? g : 0.f, s + 2 < S ? g : 0.f,
+                                s + 3 < S ? g : 0.f);
+      f.v[2 * it + 1] = make_float4(s + 4 < S ? g : 0.f, s + 5 < S ? g : 0.f,
+                                    s + 6 < S ? g : 0.f, s + 7 < S ? g : 0.f);
     }
   }
 }
@@ -510,60 +527,54 @@ __device__ __forceinline__ int rescale_exponent(float m, bool valid, int* err) {
 // from those vectors before the first level runs.
 // ---------------------------------------------------------------------------
 template <typename T>  // float only
-__global__ void __launch_bounds__(kTcThreads, 2) post_u_kernel(LevelArgs<T> a) {
+__global__ void __launch_bounds__(kTcThreads, PHYLO_POST_U_BLOCKS) post_u_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
   pdl_wait_and_release();  // before TMEM, smem or any global access
   static_assert(kStageBytes <= kOp128, "staging fits in the operand buffer");
+  static_assert(2 * kPt32Bytes <= kOp128, "staged lookup tables fit in the operand buffer");
   extern __shared__ unsigned char smraw[];
   unsigned char* base = align1024(smraw);
   unsigned char* A = base;            // p_k as three BF16 terms
   unsigned char* B = base + kOp128;   // P_k (rows = rows of P)
   float* stage = reinterpret_cast<float*>(A);  // U_k rows, after the MMAs
+  // before the split, A holds the FP32 P' of the compact children (lookups)
+  const float* pt32[2] = {reinterpret_cast<const float*>(A),
+                          reinterpret_cast<const float*>(A + kPt32Bytes)};
   __shared__ uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = tid & (kTcRows - 1), h = tid / kTcRows;
-  const int R = a.n_cat, C = a.n_patterns;
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
   const int4 d = a.level_desc[blockIdx.y];
   const int k = d.x, r = blockIdx.z;
   const int c0 = blockIdx.x * kTcRows;
-  if (warp == 0) tc::alloc(&tmem_slot, 64);
+  const bool tip = a.tip_level;
+  const TcChild xs[2] = {tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0),
+                         tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1)};
   if (tid == 0) {
     mbar_init_fenced(&bar_tma, 1);
     mbar_init_fenced(&bar_mma, 1);
-    mbar_expect_tx(&bar_tma, kOp64);
+    uint32_t bytes = kOp64;
+    if (!tip)
+      for (int x = 0; x < 2; ++x) bytes += xs[x].compact ? kPt32Bytes : 0;
+    mbar_expect_tx(&bar_tma, bytes);
     bulk_g2s(B, unit_tiles(a, k, r) + kUnitP, kOp64, &bar_tma);
+    if (!tip)
+      for (int x = 0; x < 2; ++x)
+        if (xs[x].compact)
+          bulk_g2s(A + x * kPt32Bytes, unit_tiles(a, xs[x].b, r) + kUnitPt32, kPt32Bytes,
+                   &bar_tma);
   }
-  float4 v[8];
-  if (a.tip_level) {
-    coop_load(v, a.tip_partials + (size_t)k * C * 64, 64, c0, C);
+  // every global load is issued before the first wait
+  UFetch f0, f1;
+  if (tip) {
+    coop_load(f0.v, a.tip_partials + (size_t)k * C * 64, 64, c0, C);
   } else {
-    // p_k = U_i o U_j, each row rescaled into [1/2, 1)
-    const TcChild x0 = tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0);
-    const TcChild x1 = tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1);
-    float4 u[8];
-    int E[4], E1[4], y[4];
-    coop_child_u(v, E, y, a, x0, r, c0);
-    coop_child_u(u, E1, y, a, x1, r, c0);
-#pragma unroll
-    for (int it = 0; it < 4; ++it) {
-      v[2 * it] = mul4(v[2 * it], u[2 * it]);
-      v[2 * it + 1] = mul4(v[2 * it + 1], u[2 * it + 1]);
-      const float m = row_max8(amax4(v[2 * it + 1], amax4(v[2 * it], 0.f)));
-      const int c = c0 + coop_row(it);
-      const int e = rescale_exponent(m, c < C, a.err);
-      const float f = ldexpf(1.f, -e);
-      v[2 * it] = make_float4(v[2 * it].x * f, v[2 * it].y * f, v[2 * it].z * f,
-                              v[2 * it].w * f);
-      v[2 * it + 1] = make_float4(v[2 * it + 1].x * f, v[2 * it + 1].y * f,
-                                  v[2 * it + 1].z * f, v[2 * it + 1].w * f);
-      if (c < C && (lane & 7) == 0)
-        a.escale[((size_t)(k - a.n_tips) * R + r) * a.escale_stride + c] = E[it] + E1[it] + e;
-    }
+    coop_child_u_issue(f0, a, xs[0], r, c0);
+    coop_child_u_issue(f1, a, xs[1], r, c0);
   }
-  coop_put(A, v);
-  tc::fence_smem_for_async();
-  __syncthreads();  // barriers initialised, TMEM allocated, p_k staged
+  if (warp == 0) tc::alloc(&tmem_slot, 64);
+  __syncthreads();  // barriers initialised, TMEM allocated
   tc::fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
@@ -571,7 +582,33 @@ __global__ void __launch_bounds__(kTcThreads, 2) post_u_kernel(LevelArgs<T> a) {
   int pend_tma = -1, pend_mma = -1;
   bool ok = tc_block_wait(&bar_tma, ptma, pend_tma, a.err);
   if (ok) {
+    if (!tip) {
+      // p_k = U_i o U_j, each row rescaled into [1/2, 1)
+      coop_child_u_finish(f0, xs[0].compact, pt32[0], S);
+      coop_child_u_finish(f1, xs[1].compact, pt32[1], S);
+#pragma unroll
+      for (int it = 0; it < 4; ++it) {
+        float4& v0 = f0.v[2 * it];
+        float4& v1 = f0.v[2 * it + 1];
+        v0 = mul4(v0, f1.v[2 * it]);
+        v1 = mul4(v1, f1.v[2 * it + 1]);
+        const float m = row_max8(amax4(v1, amax4(v0, 0.f)));
+        const int c = c0 + coop_row(it);
+        const int e = rescale_exponent(m, c < C, a.err);
+        const float sc = ldexpf(1.f, -e);
+        v0 = make_float4(v0.x * sc, v0.y * sc, v0.z * sc, v0.w * sc);
+        v1 = make_float4(v1.x * sc, v1.y * sc, v1.z * sc, v1.w * sc);
+        if (c < C && (lane & 7) == 0)
+          a.escale[((size_t)(k - a.n_tips) * R + r) * a.escale_stride + c] =
+              f0.E[it] + f1.E[it] + e;
+      }
+      __syncthreads();  // every lookup in A is done before the split overwrites it
+    }
+    coop_put(A, f0.v);
+    tc::fence_smem_for_async();
+    __syncthreads();
     if (tid == 0) {
+      tc::fence_after();
       uint32_t ta[3], tb[3];
       term_addrs(A, kTerm128, ta);
       term_addrs(B, kTerm64, tb);
@@ -680,6 +717,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
   pdl_wait_and_release();  // before TMEM, smem or any global access
   static_assert(kStageBytes <= kOp128 && kStageBytes <= 2 * kOp64, "staging fits");
+  static_assert(kPt32Bytes <= kOp64, "a lookup table fits in the P' buffer");
   extern __shared__ unsigned char smraw[];
   unsigned char* base = align1024(smraw);
   unsigned char* A = base;                     // a_x as three BF16 terms
@@ -687,6 +725,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
   unsigned char* Bq = base + kOp128 + kOp64;   // Q' (rows = columns of Q)
   float* stW = reinterpret_cast<float*>(A);    // W_x rows, after the MMAs
   float* stQ = reinterpret_cast<float*>(Bp);   // q_x rows, after the MMAs
+  // lookup tables of compact children (FP32 P'): the sibling's in A until
+  // the split, the child's own in Bp (unused by a tip child's MMA)
+  const float* pt32x = reinterpret_cast<const float*>(Bp);
+  const float* pt32y = reinterpret_cast<const float*>(A);
   __shared__ uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_slot;
   __shared__ float xch[2][kTcRows];  // the two halves' row maxima
@@ -704,17 +746,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
   const size_t kslot = (size_t)(k - a.n_tips);
   const int c0 = blockIdx.x * kTcRows;
   const int estr = a.escale_stride;
-  if (warp == 0) tc::alloc(&tmem_slot, 128);
   if (tid == 0) {
     mbar_init_fenced(&bar_tma, 1);
     mbar_init_fenced(&bar_mma, 1);
-    mbar_expect_tx(&bar_tma, cx.internal ? 2 * kOp64 : kOp64);
+    mbar_expect_tx(&bar_tma, kOp64 + (cx.internal ? kOp64 : 0) +
+                                 (cx.compact ? kPt32Bytes : 0) + (cy.compact ? kPt32Bytes : 0));
     bulk_g2s(Bq, a.qt, kOp64, &bar_tma);
     if (cx.internal) bulk_g2s(Bp, unit_tiles(a, cx.b, r) + kUnitPt, kOp64, &bar_tma);
+    if (cx.compact)
+      bulk_g2s(Bp, unit_tiles(a, cx.b, r) + kUnitPt32, kPt32Bytes, &bar_tma);
+    if (cy.compact)
+      bulk_g2s(A, unit_tiles(a, cy.b, r) + kUnitPt32, kPt32Bytes, &bar_tma);
   }
-  // every global load is issued before any is used
-  float4 q[8], ux[8], uy[8];
-  int eq[4], Ex[4], Ey[4], yx[4], yy[4];
+  // every global load is issued before the first wait
+  const float wg = (float)(a.cat_w[r] * a.rates[r]), wr = a.cat_wt[r];
+  float4 q[8];
+  int eq[4];
   if (!root) {
     coop_load(q, a.pre + (kslot * C * R + r) * 64, (size_t)R * 64, c0, C);
 #pragma unroll
@@ -738,27 +785,34 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
       eq[it] = 0;
     }
   }
-  coop_child_u(ux, Ex, yx, a, cx, r, c0);
-  coop_child_u(uy, Ey, yy, a, cy, r, c0);
-  // a_x = q_k o U_y (into q) and den = a_x . U_x per row
-  float den[4];
-#pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    q[2 * it] = mul4(q[2 * it], uy[2 * it]);
-    q[2 * it + 1] = mul4(q[2 * it + 1], uy[2 * it + 1]);
-    den[it] = row_sum8(dot4(q[2 * it + 1], ux[2 * it + 1], dot4(q[2 * it], ux[2 * it], 0.f)));
-  }
-  coop_put(A, q);
-  tc::fence_smem_for_async();
-  __syncthreads();  // barriers initialised, TMEM allocated, a_x staged
+  UFetch fx, fy;
+  coop_child_u_issue(fx, a, cx, r, c0);
+  coop_child_u_issue(fy, a, cy, r, c0);
+  if (warp == 0) tc::alloc(&tmem_slot, 128);
+  __syncthreads();  // barriers initialised, TMEM allocated
   tc::fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16);
   uint32_t ptma = 0, pmma = 0;
   int pend_tma = -1, pend_mma = -1;
   bool ok = tc_block_wait(&bar_tma, ptma, pend_tma, a.err);
+  float den[4];
   if (ok) {
+    coop_child_u_finish(fx, cx.compact, pt32x, S);
+    coop_child_u_finish(fy, cy.compact, pt32y, S);
+    // a_x = q_k o U_y (into q) and den = a_x . U_x per row
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      q[2 * it] = mul4(q[2 * it], fy.v[2 * it]);
+      q[2 * it + 1] = mul4(q[2 * it + 1], fy.v[2 * it + 1]);
+      den[it] = row_sum8(dot4(q[2 * it + 1], fx.v[2 * it + 1], dot4(q[2 * it], fx.v[2 * it], 0.f)));
+    }
+    __syncthreads();  // every lookup in A is done before the split overwrites it
+    coop_put(A, q);
+    tc::fence_smem_for_async();
+    __syncthreads();
     if (tid == 0) {  // TMEM columns [q_x | W_x]
+      tc::fence_after();
       uint32_t ta[3], tb[3];
       term_addrs(A, kTerm128, ta);
       term_addrs(Bq, kTerm64, tb);
@@ -792,25 +846,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
     }
     __syncthreads();
     // num_x = W_x . U_x per row; the Eq. 8 terms of this category
-    const float wg = (float)(a.cat_w[r] * a.rates[r]), w = a.cat_wt[r];
     float* rt = reinterpret_cast<float*>(a.rterm);
 #pragma unroll
     for (int it = 0; it < 4; ++it) {
       const int rr = coop_row(it), c = c0 + rr;
       const float4 w0 = *reinterpret_cast<const float4*>(stW + rr * kStageLd + 8 * j);
       const float4 w1 = *reinterpret_cast<const float4*>(stW + rr * kStageLd + 8 * j + 4);
-      float num = row_sum8(dot4(w1, ux[2 * it + 1], dot4(w0, ux[2 * it], 0.f)));
-      if (cx.compact && yx[it] >= S) num = 0.f;  // d/dt of the all-ones vector is 0
+      float num = row_sum8(dot4(w1, fx.v[2 * it + 1], dot4(w0, fx.v[2 * it], 0.f)));
+      if (cx.compact && fx.y[it] >= S) num = 0.f;  // d/dt of the all-ones vector is 0
       if (c < C && j == 0) {
         float* t4 = rt + ((kslot * C + c) * R + r) * 4;
         t4[x] = wg * num;
         if (x == 0) {
-          t4[2] = w * den[it];
-          t4[3] = __int_as_float(eq[it] + Ex[it] + Ey[it]);
+          t4[2] = wr * den[it];
+          t4[3] = __int_as_float(eq[it] + fx.E[it] + fy.E[it]);
         }
         if (cx.internal)  // q_x = P_x' (q_k o U_y): exponents of q_k and of U_y
           a.pre_escale[((size_t)(cx.b - a.n_tips) * R + r) * estr + c] =
-              eexp[rr] + eq[it] + Ey[it];
+              eexp[rr] + eq[it] + fy.E[it];
       }
     }
     if (cx.internal)
@@ -825,7 +878,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
   __syncthreads();
   if (warp == 0) tc::dealloc(tmem, 128);
 }
-
 
 // ---------------------------------------------------------------------------
 // Eq. 8 ratios and their per-tile sums (Eq. 7) for both children of every
