@@ -386,36 +386,12 @@ __device__ __forceinline__ void load_child(const LevelArgs<T>& a, int b,
 }
 
 // u = M v (a compact state picks column y of M; the gap code gives the
-// all-ones vector), and with WITH_D also w = dM v (0 for a gap).  With the
-// transposed layout (kTrSmall) M and dM hold M' and dM'.
+// all-ones vector), and with WITH_D also w = dM v (0 for a gap).
 template <typename T, int SP, bool WITH_D>
 __device__ __forceinline__ void child_apply(const ChildIn<T, SP>& in, int S,
                                             const T* __restrict__ M,
                                             const T* __restrict__ dM,
                                             T (&u)[SP], T (&w)[SP]) {
-  if constexpr (kTrSmall<T, SP>) {
-    if (in.y >= 0) {
-      if (in.y < S) {  // column y of M = row y of M'
-#pragma unroll
-        for (int s = 0; s < SP; ++s) u[s] = M[in.y * SP + s];
-        if constexpr (WITH_D) {
-#pragma unroll
-          for (int s = 0; s < SP; ++s) w[s] = dM[in.y * SP + s];
-        }
-      } else {
-#pragma unroll
-        for (int s = 0; s < SP; ++s) u[s] = s < S ? T(1) : T(0);
-        if constexpr (WITH_D) {
-#pragma unroll
-          for (int s = 0; s < SP; ++s) w[s] = T(0);
-        }
-      }
-      return;
-    }
-    rowcomb2<SP>(M, in.v, u);
-    if constexpr (WITH_D) rowcomb2<SP>(dM, in.v, w);
-    return;
-  }
   if (in.y >= 0) {
     if (in.y < S) {
 #pragma unroll
@@ -456,25 +432,16 @@ __device__ __forceinline__ void issue_mats(const T* __restrict__ base,
 }
 
 // Matrix slots per node of the pre-order register kernels: P_i, P_j, dP_i,
-// dP_j, or with the transposed layout P'_i, P'_j, dP'_i, dP'_j, P_i, P_j.
+// dP_j.
 template <typename T, int SP>
-constexpr int kPreSlots = kTrSmall<T, SP> ? 6 : 4;
+constexpr int kPreSlots = 4;
 
 constexpr int kDescCompactX = kDescFlagCompact0, kDescCompactY = kDescFlagCompact1;
-
-// Resident blocks asked of the register allocator: the FP32 20-state
-// kernels hold three 20-element vectors per input and run latency-bound.
-// On the 256-taxon amino-acid workload, capping the pre-order kernel at 3
-// blocks (168 registers) measured 12% faster than the unbounded 212
-// registers (2 blocks); 4 blocks spilled and was slower.  The post-order
-// kernel runs 4% faster at 4 blocks (127 registers) than at 3.
-template <typename T, int SP, bool PRE>
-constexpr int kSmallMinBlocks = (SP == 20 && sizeof(T) == 4) ? (PRE ? 3 : 4) : 0;
 
 // Post-order level (Eq. 2): p_k = (P_i p_i) o (P_j p_j), rescaled; at the
 // root also log P(Y_c) (Eq. 3) weighted by W_c and summed per tile.
 template <typename T, int SP, int RP, int NPT>
-__global__ void __launch_bounds__(kSmallThreads, kSmallMinBlocks<T, SP, false>)
+__global__ void __launch_bounds__(kSmallThreads)
 post_small_kernel(LevelArgs<T> a) {
   constexpr int NT = kSmallThreads, CT = NT / RP;
   constexpr int MS = MatStride<T, SP>::v;
@@ -501,8 +468,7 @@ post_small_kernel(LevelArgs<T> a) {
     int br[2 * NPT];
     for (int u = 0; u < nn; ++u) { br[2 * u] = d[u].y; br[2 * u + 1] = d[u].z; }
     mbar_expect_tx(&bar, (uint32_t)(2 * nn * R * SP * SP * sizeof(T)));
-    // (transposed layout: P' is kind 0 of each branch)
-    issue_mats<T, SP, RP>(a.P, br, 2 * nn, R, mats, &bar, kTrSmall<T, SP> ? kP4MatKinds : 1, 0);
+    issue_mats<T, SP, RP>(a.P, br, 2 * nn, R, mats, &bar);
   }
   ChildIn<T, SP> in[NPT][2];
 #pragma unroll
@@ -562,7 +528,7 @@ post_small_kernel(LevelArgs<T> a) {
 // stored (rescaled) for internal children; the ratio for branches i and j
 // is reduced over the tile's patterns with weights W_c (Eq. 7).
 template <typename T, int SP, int RP, int NPT>
-__global__ void __launch_bounds__(kSmallThreads, kSmallMinBlocks<T, SP, true>)
+__global__ void __launch_bounds__(kSmallThreads)
 pre_small_kernel(LevelArgs<T> a) {
   constexpr int NT = kSmallThreads, CT = NT / RP;
   constexpr int MS = MatStride<T, SP>::v;
@@ -593,14 +559,8 @@ pre_small_kernel(LevelArgs<T> a) {
       br[0] = d[u].y;
       br[1] = d[u].z;
       T* slots = mats + (size_t)(NS * u) * RP * MS;
-      if constexpr (kTrSmall<T, SP>) {
-        for (int kind = 0; kind < kP4MatKinds; ++kind)
-          issue_mats<T, SP, RP>(a.P, br, 2, R, slots + (size_t)(2 * kind) * RP * MS, &bar,
-                                kP4MatKinds, kind);
-      } else {
-        issue_mats<T, SP, RP>(a.P, br, 2, R, slots, &bar);
-        issue_mats<T, SP, RP>(a.dP, br, 2, R, slots + (size_t)2 * RP * MS, &bar);
-      }
+      issue_mats<T, SP, RP>(a.P, br, 2, R, slots, &bar);
+      issue_mats<T, SP, RP>(a.dP, br, 2, R, slots + (size_t)2 * RP * MS, &bar);
     }
   }
   T q[NPT][SP];
@@ -632,13 +592,10 @@ pre_small_kernel(LevelArgs<T> a) {
   for (int u = 0; u < NPT; ++u) {
     if (u >= nn) break;
     const int bi = d[u].y, bj = d[u].z;
-    const T* Pi = mats + ((NS * u) * RP + rr) * MS;  // (transposed layout: P'_i)
+    const T* Pi = mats + ((NS * u) * RP + rr) * MS;
     const T* Pj = mats + ((NS * u + 1) * RP + rr) * MS;
     const T* Di = mats + ((NS * u + 2) * RP + rr) * MS;
     const T* Dj = mats + ((NS * u + 3) * RP + rr) * MS;
-    // the rows of P_i, P_j for Eq. 4
-    const T* Ri = kTrSmall<T, SP> ? mats + ((NS * u + 4) * RP + rr) * MS : Pi;
-    const T* Rj = kTrSmall<T, SP> ? mats + ((NS * u + 5) * RP + rr) * MS : Pj;
     T ui[SP], vi[SP], uj[SP], vj[SP];
     child_apply<T, SP, true>(in[u][0], a.n_states, Pi, Di, ui, vi);
     child_apply<T, SP, true>(in[u][1], a.n_states, Pj, Dj, uj, vj);
@@ -671,8 +628,7 @@ pre_small_kernel(LevelArgs<T> a) {
       T av[SP], out[SP];
 #pragma unroll
       for (int s = 0; s < SP; ++s) av[s] = q[u][s] * uj[s];
-      if constexpr (kTrSmall<T, SP>) rowcomb2<SP>(Ri, av, out);
-      else matvec_t<T, SP>(Ri, av, out);
+      matvec_t<T, SP>(Pi, av, out);
       const T m = pattern_max<T, SP, RP>(out, active);
       rescale<T, SP>(out, m, valid_c, a.err);
       if (active) {
@@ -684,8 +640,7 @@ pre_small_kernel(LevelArgs<T> a) {
       T av[SP], out[SP];
 #pragma unroll
       for (int s = 0; s < SP; ++s) av[s] = q[u][s] * ui[s];
-      if constexpr (kTrSmall<T, SP>) rowcomb2<SP>(Rj, av, out);
-      else matvec_t<T, SP>(Rj, av, out);
+      matvec_t<T, SP>(Pj, av, out);
       const T m = pattern_max<T, SP, RP>(out, active);
       rescale<T, SP>(out, m, valid_c, a.err);
       if (active) {
@@ -707,6 +662,319 @@ pre_small_kernel(LevelArgs<T> a) {
     }
     __syncthreads();  // red[] is reused by the next node
   }
+}
+
+// ---------------------------------------------------------------------------
+// FP32 with 20 padded states (amino-acid models): the post-order pass stores,
+// for every non-root node x with stored partials, U_x = P_x p_x -- the
+// factor x contributes to its parent in Eq. 2 -- instead of p_x, and a
+// node's p is formed from its children's U when its own step runs:
+//   post:  p_k = U_i o U_j (rescaled);  U_k = P_k p_k stored   (Eq. 2)
+//   root:  log sum_r w_r pi' p_root                             (Eq. 3)
+//   pre:   a_i = q_k o U_j,  a_j = q_k o U_i,  den = a_i . U_i
+//          num_x = gamma_r (a_x' Q) U_x  (a tip: a_x' dP_x e_y)  (Eq. 8)
+//          q_x = P_x' a_x for internal children                 (Eq. 4)
+// Eq. 8's numerator q_x' Q p_x (times gamma_r) equals a_x' P_x Q p_x =
+// (a_x' Q)(P_x p_x) because P_x = exp(gamma_r t_x Q) commutes with Q, so an
+// internal child costs two products in the pre-order step (Q' a and P' a)
+// instead of three (P p, dP p, P' a).  U costs the post-order pass the bytes
+// that storing p did.  Layouts as in the register kernels above (tile-blocked
+// vectors; matrices [P' | dP' | P] per branch); tips with partial vectors
+// keep their U in slots N - 1 + x of the post region, formed by a first
+// launch over those tips (`tip_level`).
+// ---------------------------------------------------------------------------
+constexpr int kU20 = 20;
+
+// U slot of node x: internal nodes x - N, tips with partials N - 1 + x.
+__device__ __forceinline__ size_t u20_slot(const LevelArgs<float>& a, int x) {
+  return x >= a.n_tips ? (size_t)(x - a.n_tips) : (size_t)(a.n_tips - 1 + x);
+}
+
+// A child's U row for this thread's (pattern, category): stored (internal
+// child or tip with partials, with the child's exponent) or, for a compact
+// tip, its state (resolved by u20_resolve from the staged P').
+template <int RP>
+__device__ __forceinline__ void load_u20(const LevelArgs<float>& a, int b, bool compact, int c,
+                                         int r, bool active, bool want_e,
+                                         ChildIn<float, kU20>& in) {
+  using SV = SmallVec<float, kU20, RP>;
+  in.e = 0;
+  if (compact) {
+    in.y = active ? (int)a.tip_states[(size_t)b * a.state_stride + c] : 0;
+    return;
+  }
+  in.y = -1;
+  load_vec<float, kU20>(
+      a.post + SV::offset(u20_slot(a, b), c, r, a.n_cat, a.n_patterns, a.n_tiles), in.v,
+      active, SV::cs);
+  if (want_e && active && b >= a.n_tips)
+    in.e = a.escale[(size_t)(b - a.n_tips) * a.escale_stride + c];
+}
+
+// U of a child: the loaded row, or column y of P (row y of P' = Pt); a gap
+// selects the all-ones vector.
+__device__ __forceinline__ void u20_resolve(const ChildIn<float, kU20>& in, int S,
+                                            const float* __restrict__ Pt, float (&u)[kU20]) {
+  if (in.y < 0) {
+#pragma unroll
+    for (int s = 0; s < kU20; ++s) u[s] = in.v[s];
+  } else if (in.y < S) {
+#pragma unroll
+    for (int s = 0; s < kU20; ++s) u[s] = Pt[in.y * kU20 + s];
+  } else {
+#pragma unroll
+    for (int s = 0; s < kU20; ++s) u[s] = s < S ? 1.f : 0.f;
+  }
+}
+
+// Resident blocks of the U-form kernels' register bound.
+#ifndef PHYLO_U20_POST_BLOCKS
+#define PHYLO_U20_POST_BLOCKS 4
+#endif
+#ifndef PHYLO_U20_PRE_BLOCKS
+#define PHYLO_U20_PRE_BLOCKS 4
+#endif
+
+// Post-order level: per node of the block, slots [P'_child0 | P'_child1 |
+// P'_node] (every category); on the tip level, P'_tip alone.
+template <int RP, int NPT>
+__global__ void __launch_bounds__(kSmallThreads, PHYLO_U20_POST_BLOCKS)
+post_u20_kernel(LevelArgs<float> a) {
+  constexpr int SP = kU20, NT = kSmallThreads, CT = NT / RP;
+  constexpr int MS = MatStride<float, SP>::v;
+  using SV = SmallVec<float, SP, RP>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* mats = reinterpret_cast<float*>(smraw);  // [NPT][3][RP][MS]
+  __shared__ uint64_t bar;
+  __shared__ double red[NT / 32][2];
+  const int g0 = blockIdx.y * NPT;
+  const int nn = min(NPT, a.n_level - g0);
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int c = blockIdx.x * CT + threadIdx.x / RP;
+  const int r = threadIdx.x % RP;
+  const bool valid_c = c < C;
+  const bool active = valid_c && r < R;
+  const int rr = r < R ? r : 0;
+  const bool tip = a.tip_level;
+  if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
+  __syncthreads();
+  pdl_wait_and_release();
+  int4 d[NPT];
+#pragma unroll
+  for (int u = 0; u < NPT; ++u)
+    d[u] = u < nn ? a.level_desc[g0 + u] : make_int4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    uint32_t nmat = 0;
+    for (int u = 0; u < nn; ++u) nmat += tip ? 1 : (d[u].x == a.root ? 2 : 3);
+    mbar_expect_tx(&bar, nmat * (uint32_t)(R * SP * SP * sizeof(float)));
+    for (int u = 0; u < nn; ++u) {
+      float* slots = mats + (size_t)(3 * u) * RP * MS;
+      const int br[3] = {d[u].y, d[u].z, d[u].x};
+      for (int x = tip ? 2 : 0; x < 3; ++x)
+        if (x < 2 || d[u].x != a.root)
+          issue_mats<float, SP, RP>(a.P, br + x, 1, R, slots + (size_t)x * RP * MS, &bar,
+                                    kP4MatKinds, 0);
+    }
+  }
+  ChildIn<float, SP> in[NPT][2];
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    if (u >= nn) continue;
+    if (tip) {  // the tip's partial vector
+      in[u][0].y = -1;
+      in[u][0].e = 0;
+      load_vec<float, SP>(a.tip_partials + ((size_t)d[u].x * C + c) * SP, in[u][0].v, active);
+    } else {
+      load_u20<RP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, true, in[u][0]);
+      load_u20<RP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, true, in[u][1]);
+    }
+  }
+  if (!__syncthreads_and(mbar_wait(&bar, 0))) {
+    if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    if (u >= nn) break;
+    const int k = d[u].x;
+    const float* Ptk = mats + ((3 * u + 2) * RP + rr) * MS;
+    float p[SP], uk[SP];
+    int e = 0;
+    if (tip) {
+#pragma unroll
+      for (int s = 0; s < SP; ++s) p[s] = in[u][0].v[s];
+    } else {
+      float uj[SP];
+      u20_resolve(in[u][0], S, mats + ((3 * u) * RP + rr) * MS, p);
+      u20_resolve(in[u][1], S, mats + ((3 * u + 1) * RP + rr) * MS, uj);
+#pragma unroll
+      for (int s = 0; s < SP; ++s) p[s] *= uj[s];
+      const float m = pattern_max<float, SP, RP>(p, active);
+      e = rescale<float, SP>(p, m, valid_c, a.err) + in[u][0].e + in[u][1].e;
+    }
+    if (k != a.root) {
+      rowcomb2<SP>(Ptk, p, uk);  // U_k = P_k p_k
+      if (active) {
+        store_vec<float, SP>(a.post + SV::offset(u20_slot(a, k), c, r, R, C, a.n_tiles), uk,
+                             SV::cs);
+        if (!tip && r == 0) a.escale[(size_t)(k - a.n_tips) * a.escale_stride + c] = e;
+      }
+      continue;
+    }
+    // Root: L_c = sum_r w_r pi' p_root (Eq. 3), with the exponents restored.
+    double lr = 0.0;
+    if (active) {
+#pragma unroll
+      for (int s = 0; s < SP; ++s)
+        if (s < S) lr += a.root_pi[s] * (double)p[s];
+      lr *= a.cat_w[r];
+    }
+    lr = sum_over_lanes<RP>(lr);
+    double term = 0.0, unused = 0.0;
+    if (valid_c && r == 0) {
+      if (!(lr > 0.0) || !isfinite(lr)) atomicOr(a.err, ERR_ZERO_PARTIAL);
+      term = a.pattern_w[c] * (log(lr) + (double)e * 0.69314718055994530942);
+    }
+    block_sum2<NT>(term, unused, red);
+    if (threadIdx.x == 0) a.lpart[blockIdx.x] = term;
+  }
+}
+
+// Pre-order level with the fused gradient: slots per node [P'_i | P'_j |
+// dP'_i | dP'_j | P_i | P_j] (every category), then Q (one matrix).
+template <int RP, int NPT>
+__global__ void __launch_bounds__(kSmallThreads, PHYLO_U20_PRE_BLOCKS)
+pre_u20_kernel(LevelArgs<float> a) {
+  constexpr int SP = kU20, NT = kSmallThreads, CT = NT / RP;
+  constexpr int MS = MatStride<float, SP>::v;
+  constexpr int NS = 6;
+  using SV = SmallVec<float, SP, RP>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* mats = reinterpret_cast<float*>(smraw);  // [NPT][NS][RP][MS]
+  float* Qm = mats + (size_t)NPT * NS * RP * MS;  // Q, row-major SP x SP
+  __shared__ uint64_t bar;
+  __shared__ F2 red[NT / 32][2];
+  const int g0 = blockIdx.y * NPT;
+  const int nn = min(NPT, a.n_level - g0);
+  const int R = a.n_cat, C = a.n_patterns, S = a.n_states;
+  const int c = blockIdx.x * CT + threadIdx.x / RP;
+  const int r = threadIdx.x % RP;
+  const bool valid_c = c < C;
+  const bool active = valid_c && r < R;
+  const int rr = r < R ? r : 0;
+  if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
+  __syncthreads();
+  pdl_wait_and_release();
+  int4 d[NPT];
+#pragma unroll
+  for (int u = 0; u < NPT; ++u)
+    d[u] = u < nn ? a.level_desc[g0 + u] : make_int4(0, 0, 0, 0);
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar, (uint32_t)((NS * nn * R + 1) * SP * SP * sizeof(float)));
+    bulk_g2s(Qm, a.qmat, (uint32_t)(SP * SP * sizeof(float)), &bar);
+    for (int u = 0; u < nn; ++u) {
+      const int br[2] = {d[u].y, d[u].z};
+      float* slots = mats + (size_t)(NS * u) * RP * MS;
+      for (int kind = 0; kind < kP4MatKinds; ++kind)
+        issue_mats<float, SP, RP>(a.P, br, 2, R, slots + (size_t)(2 * kind) * RP * MS, &bar,
+                                  kP4MatKinds, kind);
+    }
+  }
+  float q[NPT][SP];
+  ChildIn<float, SP> in[NPT][2];
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    if (u >= nn) continue;
+    const int k = d[u].x;
+    if (k == a.root) {
+#pragma unroll
+      for (int s = 0; s < SP; ++s) q[u][s] = (active && s < S) ? a.root_pit[s] : 0.f;
+    } else {
+      load_vec<float, SP>(a.pre + SV::offset(k - a.n_tips, c, r, R, C, a.n_tiles), q[u], active,
+                          SV::cs);
+    }
+    load_u20<RP>(a, d[u].y, d[u].w & kDescCompactX, c, r, active, false, in[u][0]);
+    load_u20<RP>(a, d[u].z, d[u].w & kDescCompactY, c, r, active, false, in[u][1]);
+  }
+  const float w = active ? a.cat_wt[r] : 0.f;
+  const float gam = active ? (float)a.rates[r] : 0.f;
+  if (!__syncthreads_and(mbar_wait(&bar, 0))) {
+    if (threadIdx.x == 0) atomicOr(a.err, ERR_TIMEOUT);
+    return;
+  }
+  using A = Acc<float>;
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    if (u >= nn) break;
+    const int b[2] = {d[u].y, d[u].z};
+    float ux[2][SP];
+    u20_resolve(in[u][0], S, mats + ((NS * u) * RP + rr) * MS, ux[0]);
+    u20_resolve(in[u][1], S, mats + ((NS * u + 1) * RP + rr) * MS, ux[1]);
+    float den = 0.f;
+#pragma unroll
+    for (int s = 0; s < SP; ++s) den = fmaf(q[u][s] * ux[1][s], ux[0][s], den);
+    float num[2];
+    typename A::type g[2];
+#pragma unroll
+    for (int x = 0; x < 2; ++x) {
+      float av[SP];  // a_x = q_k o U_y
+#pragma unroll
+      for (int s = 0; s < SP; ++s) av[s] = q[u][s] * ux[1 - x][s];
+      const int y = in[u][x].y;
+      float nx = 0.f;
+      if (y >= 0) {  // compact tip: a_x' dP_x e_y, from row y of dP' (0 for a gap)
+        if (y < S) {
+          const float* Dt = mats + ((NS * u + 2 + x) * RP + rr) * MS;
+#pragma unroll
+          for (int s = 0; s < SP; ++s) nx = fmaf(av[s], Dt[y * SP + s], nx);
+        }
+      } else {       // gamma_r (a_x' Q) U_x
+        float wq[SP];
+        rowcomb2<SP>(Qm, av, wq);
+#pragma unroll
+        for (int s = 0; s < SP; ++s) nx = fmaf(wq[s], ux[x][s], nx);
+        nx *= gam;
+      }
+      num[x] = nx;
+      if (b[x] >= a.n_tips) {  // q_x = P_x' a_x, rescaled (only ratios use it)
+        float out[SP];
+        rowcomb2<SP>(mats + ((NS * u + 4 + x) * RP + rr) * MS, av, out);
+        const float m = pattern_max<float, SP, RP>(out, active);
+        rescale<float, SP>(out, m, valid_c, a.err);
+        if (active)
+          store_vec<float, SP>(a.pre + SV::offset(b[x] - a.n_tips, c, r, R, C, a.n_tiles), out,
+                               SV::cs);
+      }
+    }
+    // sum over categories (Eq. 8) in FP32, then the ratio
+    const float Ni = sum_over_lanes<RP>(w * num[0]);
+    const float Nj = sum_over_lanes<RP>(w * num[1]);
+    const float D = sum_over_lanes<RP>(w * den);
+    g[0] = A::zero();
+    g[1] = A::zero();
+    if (valid_c && r == 0) {
+      if (!(D > 0.f) || !isfinite(D)) {
+        atomicOr(a.err, ERR_BAD_RATIO);
+      } else {
+        const float W = a.pattern_wt[c];
+        g[0] = A::prod(W, Ni / D);
+        g[1] = A::prod(W, Nj / D);
+      }
+    }
+    block_sum_acc<float, NT>(g[0], g[1], red, RP);
+    if (threadIdx.x == 0) {  // the pair as stored (the reduction converts to FP64)
+      float2* gp = reinterpret_cast<float2*>(a.gpart);
+      gp[(size_t)b[0] * a.n_tiles + blockIdx.x] = make_float2(g[0].hi, g[0].lo);
+      gp[(size_t)b[1] * a.n_tiles + blockIdx.x] = make_float2(g[1].hi, g[1].lo);
+    }
+    __syncthreads();  // red[] is reused by the next node
+  }
+}
+
+template <int RP, int NPT>
+constexpr size_t u20_smem(bool post) {
+  return ((size_t)NPT * (post ? 3 : 6) * RP + (post ? 0 : 1)) * MatStride<float, kU20>::v *
+         sizeof(float);
 }
 
 // ---------------------------------------------------------------------------
@@ -1091,6 +1359,16 @@ constexpr size_t small_smem(bool post) {
 template <typename T, int SP, int RP>
 cudaError_t launch_small(const LevelArgs<T>& a, bool post, cudaStream_t st) {
   constexpr int NPo = SmallNpt<T, SP>::post, NPr = SmallNpt<T, SP>::pre;
+  if constexpr (kTrSmall<T, SP>) {  // FP32, 20 padded states: the U form
+    if (post) {
+      dim3 grid(a.n_tiles, (a.n_level + NPo - 1) / NPo);
+      return launch_pdl(post_u20_kernel<RP, NPo>, grid, kSmallThreads, u20_smem<RP, NPo>(true),
+                        st, a);
+    }
+    dim3 grid(a.n_tiles, (a.n_level + NPr - 1) / NPr);
+    return launch_pdl(pre_u20_kernel<RP, NPr>, grid, kSmallThreads, u20_smem<RP, NPr>(false), st,
+                      a);
+  }
   if (post) {
     dim3 grid(a.n_tiles, (a.n_level + NPo - 1) / NPo);
     return launch_pdl(post_small_kernel<T, SP, RP, NPo>, grid, kSmallThreads,
@@ -1104,6 +1382,15 @@ cudaError_t launch_small(const LevelArgs<T>& a, bool post, cudaStream_t st) {
 template <typename T, int SP, int RP>
 cudaError_t prepare_small() {
   constexpr int NPo = SmallNpt<T, SP>::post, NPr = SmallNpt<T, SP>::pre;
+  if constexpr (kTrSmall<T, SP>) {
+    cudaError_t e = cudaFuncSetAttribute(post_u20_kernel<RP, NPo>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)u20_smem<RP, NPo>(true));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(pre_u20_kernel<RP, NPr>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)u20_smem<RP, NPr>(false));
+  }
   cudaError_t e = cudaFuncSetAttribute(
       post_small_kernel<T, SP, RP, NPo>, cudaFuncAttributeMaxDynamicSharedMemorySize,
       (int)small_smem<T, SP, RP, NPo>(true));

@@ -731,7 +731,6 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
   const float* pt32y = reinterpret_cast<const float*>(A);
   __shared__ uint64_t bar_tma, bar_mma;
   __shared__ uint32_t tmem_slot;
-  __shared__ float xch[2][kTcRows];  // the two halves' row maxima
   __shared__ int eexp[kTcRows];      // each row's rescale exponent of q_x
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, j = lane & 7;
   const int row = tid & (kTcRows - 1), h = tid / kTcRows;
@@ -759,7 +758,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
       bulk_g2s(A, unit_tiles(a, cy.b, r) + kUnitPt32, kPt32Bytes, &bar_tma);
   }
   // every global load is issued before the first wait
-  const float wg = (float)(a.cat_w[r] * a.rates[r]), wr = a.cat_wt[r];
+  const double cw = a.cat_w[r], rate = a.rates[r];  // used in the epilogue
+  const float wr = a.cat_wt[r];
   float4 q[8];
   int eq[4];
   if (!root) {
@@ -826,26 +826,34 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
     ok = tc_block_wait(&bar_mma, pmma, pend_mma, a.err);
   }
   if (ok) {
-    {
-      float w[32];
-      tc::ld32(trow + 64 + 32 * h, w);
-      stage_half(stW, row, h, w, 1.f);
-    }
-    if (cx.internal) {  // q_x = a_x P_x, each row rescaled into [1/2, 1)
-      float qo[32];
-      tc::ld32(trow + 32 * h, qo);
+    // the second half of the threads stages W_x, the first half q_x (one
+    // thread per row: the row maximum needs no exchange)
+    if (h == 1) {
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        float w[32];
+        tc::ld32(trow + 64 + 32 * hh, w);
+#pragma unroll
+        for (int i = 0; i < 32; i += 4)
+          *reinterpret_cast<float4*>(stW + row * kStageLd + 32 * hh + i) =
+              make_float4(w[i], w[i + 1], w[i + 2], w[i + 3]);
+      }
+    } else if (cx.internal) {  // q_x = a_x P_x, each row rescaled into [1/2, 1)
+      float q0[32], q1[32];
+      tc::ld32(trow, q0);
+      tc::ld32(trow + 32, q1);
       float m = 0.f;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) m = fmaxf(m, fabsf(qo[i]));
-      xch[h][row] = m;
-      __syncthreads();
-      m = fmaxf(m, xch[1 - h][row]);
+      for (int i = 0; i < 32; ++i) m = fmaxf(m, fmaxf(fabsf(q0[i]), fabsf(q1[i])));
       const int e = rescale_exponent(m, c0 + row < C, a.err);
-      stage_half(stQ, row, h, qo, ldexpf(1.f, -e));
-      if (h == 0) eexp[row] = e;
+      const float f = ldexpf(1.f, -e);
+      stage_half(stQ, row, 0, q0, f);
+      stage_half(stQ, row, 1, q1, f);
+      eexp[row] = e;
     }
     __syncthreads();
     // num_x = W_x . U_x per row; the Eq. 8 terms of this category
+    const float wg = (float)(cw * rate);
     float* rt = reinterpret_cast<float*>(a.rterm);
 #pragma unroll
     for (int it = 0; it < 4; ++it) {

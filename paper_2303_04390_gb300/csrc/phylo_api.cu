@@ -45,8 +45,9 @@ struct Layout {
   Region vsplit;  // tensor-core path: eigenvectors as double-float tables
   Region tc_tiles;  // 65..128 states, FP32: pre-split matrix blocks
   Region qt;        // 21..64 states, FP32: Q' as a tensor-core operand
-  Region tip_desc;  // 21..64 states, FP32, with tip partials: descriptors of
-                    // the tips whose U = P p the first post-order launch forms
+  Region qmat;      // 20 padded states, FP32: Q row-major
+  Region tip_desc;  // U-form paths with tip partials: descriptors of the tips
+                    // whose U = P p the first post-order launch forms
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
   Region gpart, lpart, out;  // out = [logL, grad...] followed by the flag word
   Region chain_a, chain_b, chain_out, chain_idx;  // chain-rule epilogue staging
@@ -107,7 +108,8 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
     if (!mul_ok(n_br * R, kTcbUnitBytes, &tmp)) return "size overflow";
     ok &= add_region(L, L.tc_tiles, tmp);
   }
-  if (tc && (flags & PHYLO_FLAG_TIP_PARTIALS)) {
+  const bool uform = uses_u_form(L.SP, prec == PHYLO_FP64);
+  if (uform && (flags & PHYLO_FLAG_TIP_PARTIALS)) {
     // the post region holds U = P p of every internal node, then of every tip
     if (!mul_ok(n_int + N, per_node, &tmp) || !mul_ok(tmp, L.elem, &tmp2))
       return "size overflow";
@@ -118,6 +120,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   }
   ok &= add_region(L, L.pre, part);
   if (tc) ok &= add_region(L, L.qt, kTcQtBytes);
+  if (uform && L.SP == 20) ok &= add_region(L, L.qmat, (size_t)L.SP * L.SP * sizeof(float));
   if (C > (1 << 30)) return "n_patterns too large";
   const int planes = escale_planes(L.SP, R, prec == PHYLO_FP64);
   if (!mul_ok(n_int * planes, (size_t)round_up(C, 4) * sizeof(int), &tmp))
@@ -296,6 +299,7 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.err = reinterpret_cast<int*>(ctx->dev<double>(ctx->L.out) + 2 * ctx->N - 1);
   a.tc_tiles = ctx->L.tc_tiles.bytes ? ctx->dev<unsigned char>(ctx->L.tc_tiles) : nullptr;
   a.qt = ctx->L.qt.bytes ? ctx->dev<unsigned char>(ctx->L.qt) : nullptr;
+  a.qmat = ctx->L.qmat.bytes ? ctx->dev<float>(ctx->L.qmat) : nullptr;
   a.rates = ctx->dev<double>(ctx->L.rates);
   a.tip_level = 0;
   return a;
@@ -343,7 +347,7 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
     const int4* desc = ctx->dev<int4>(post ? ctx->L.post_desc : ctx->L.pre_desc);
     const std::vector<int>& off = post ? ctx->post_off : ctx->pre_off;
     if (post && ctx->L.tip_desc.bytes && a.tip_partials) {
-      // tensor-core path: U = P p of the tips with partials, before level 1
+      // U-form paths: U = P p of the tips with partials, before level 1
       NvtxRange range("phylo post-order tips with partials (Eq. 2)");
       LevelArgs<T> at = a;
       at.level_desc = ctx->dev<int4>(ctx->L.tip_desc);
@@ -954,6 +958,12 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
     std::vector<float> split(eigen_split_floats(ctx->L.SP));
     ctx->eig_reversible = build_eigen_split(S, ctx->L.SP, V, Vinv, pi, split.data());
     if ((rc = upload(ctx, ctx->L.vsplit, split.data(), split.size(), "upload V split"))) return rc;
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+  }
+  if (ctx->L.qmat.bytes) {
+    std::vector<float> qm((size_t)ctx->L.SP * ctx->L.SP);
+    build_q_matrix(S, ctx->L.SP, V, Vinv, lambda, qm.data());
+    if ((rc = upload(ctx, ctx->L.qmat, qm.data(), qm.size(), "upload Q"))) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }
   if (ctx->L.qt.bytes) {

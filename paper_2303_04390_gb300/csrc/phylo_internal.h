@@ -126,6 +126,25 @@ inline void build_qt_tile(int S, const double* V, const double* Vinv, const doub
     }
 }
 
+// FP32 paths whose post-order pass stores U = P p per node instead of p
+// (20 padded states, kernels.cuh; 21..64 states, kernels_tc64.cuh): tips
+// with partial vectors keep their U in extra slots of the post region, and
+// the pre-order step forms Eq. 8's numerator through Q.
+inline bool uses_u_form(int SP, bool fp64) { return (SP == 20 || SP == 64) && !fp64; }
+
+// Q = V diag(lambda) Vinv in FP64, rounded once to FP32, row-major SP x SP
+// with zero padding (the 20-state U form's pre-order step).
+inline void build_q_matrix(int S, int SP, const double* V, const double* Vinv,
+                           const double* lambda, float* out) {
+  for (int i = 0; i < SP * SP; ++i) out[i] = 0.f;
+  for (int t = 0; t < S; ++t)
+    for (int s = 0; s < S; ++s) {
+      double q = 0.0;
+      for (int m = 0; m < S; ++m) q += V[t * S + m] * lambda[m] * Vinv[m * S + s];
+      out[t * SP + s] = (float)q;
+    }
+}
+
 // FP32 with 65..128 states runs on the tensor cores too (kernels_tcb.cuh):
 // 128-pattern tiles, per-category exponents, and the matrices written by
 // the matrix kernel directly as 64 x 64 BF16 operand blocks (kind P, dP, P'
@@ -228,8 +247,8 @@ struct LevelArgs {
                                // the tensor-core and FP32 4-state paths,
                                // whose P region holds dP)
   T* post;                     // [N-1][C][R][SP] post-order partials (FP32,
-                               // 21..64 states: U = P p of every internal
-                               // node, then of every tip with partials)
+                               // 20 and 64 padded states: U = P p of every
+                               // internal node, then of every tip with partials)
   T* pre;                      // [N-1][C][R][SP] pre-order partials
   int* escale;                 // [N-1][planes][escale_stride] cumulative
                                // post-order exponents (planes: escale_planes)
@@ -255,9 +274,10 @@ struct LevelArgs {
   const unsigned char* tc_tiles;  // 65..128 states, FP32: the pre-split matrix
                                   // blocks [2N-2][R][kTcbUnitBytes] (else null)
   const unsigned char* qt;     // 21..64 states, FP32: Q' operand (kTcQtBytes)
+  const float* qmat;           // 20 padded states, FP32: Q row-major [20][20]
   const double* rates;         // [R] category rates gamma_r
-  int tip_level;               // 21..64 states, FP32: the level's nodes are tips
-                               // with partials (their U = P p, before level 1)
+  int tip_level;               // U-form paths: the level's nodes are tips with
+                               // partials (their U = P p, before level 1)
 };
 
 struct PmatArgs {

@@ -58,7 +58,7 @@ struct NaLayout {
   int SP = 0, RP = 0, n_tiles = 0;
   NaRegion children, post_nodes, pre_nodes, post_desc, pre_desc, P, dP, post, pre, escale,
       pre_escale, rterm;
-  NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t, vsplit, qt;
+  NaRegion tip_states, pattern_w, V, Vinv, lambda, pi, rates, cat_w, t, vsplit, qt, qmat;
   NaRegion gpart, lpart, out, pattern_wt, cat_wt, pi_t;
   size_t total = 0;
 };
@@ -100,6 +100,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
     na_add(L, L.rterm, n_int * (size_t)C * R * 16);
     na_add(L, L.qt, kTcQtBytes);
   }
+  if (L.SP == 20) na_add(L, L.qmat, (size_t)L.SP * L.SP * sizeof(float));
   na_add(L, L.tip_states, (size_t)N * tip_state_stride(C));
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
@@ -319,6 +320,11 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
     reversible = build_eigen_split(S, L.SP, V, Vinv, root_freqs, vsplit);
     NA_TRY(up(L.vsplit, vsplit, eigen_split_floats(L.SP) * sizeof(float)), "upload V split");
   }
+  static thread_local float qmat[20 * 20];
+  if (L.qmat.bytes) {
+    build_q_matrix(S, L.SP, V, Vinv, lambda, qmat);
+    NA_TRY(up(L.qmat, qmat, L.qmat.bytes), "upload Q");
+  }
   static thread_local unsigned char qt[kTcQtBytes];
   if (L.qt.bytes) {
     build_qt_tile(S, V, Vinv, lambda, qt);
@@ -389,6 +395,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   a.n_tiles = L.n_tiles;
   a.err = flag;
   a.qt = L.qt.bytes ? reinterpret_cast<const unsigned char*>(ws + L.qt.off) : nullptr;
+  a.qmat = L.qmat.bytes ? reinterpret_cast<const float*>(ws + L.qmat.off) : nullptr;
   a.rates = reinterpret_cast<const double*>(ws + L.rates.off);
   a.tip_level = 0;
   const int* dpost = reinterpret_cast<const int*>(ws + L.post_nodes.off);
