@@ -91,13 +91,13 @@ def algorithmic_flops(w, precision="fp32"):
     matrix-vector product of one pattern and category).  A tip child's
     P p is a column lookup, so in the form of Eq. 8 with dP p only internal
     non-root nodes count: post-order P p once (by the parent), pre-order
-    P p, dP p and P' a.  The tensor-core form for 21..64 states (FP32)
+    P p, dP p and P' a.  The tensor-core form for 21..128 states (FP32)
     stores U = P p in the post-order pass and writes Eq. 8's numerator
     through dP = gamma Q P, so its pre-order pass needs P' a of every
     internal child and Q' a of every child, tips included."""
     N, C, S, R = w.n_tips, w.n_patterns, w.n_states, w.n_categories
     node = 2 * S * S * R * C
-    if precision == "fp32" and 20 < S <= 64:
+    if precision == "fp32" and 20 < S <= 128:
         return {"pmat": 0, "post": node * (N - 2),
                 "pre": node * ((N - 2) + (2 * N - 2)), "reduce": 0}
     return {"pmat": 0, "post": node * (N - 2), "pre": 3 * node * (N - 2), "reduce": 0}
@@ -582,7 +582,7 @@ def rooflines(w, precision, phase_ms, level_counts, peaks, n_sm, workload):
     if precision == "fp32" and 64 < w.n_states <= 128:
         kernels = {"pmat": "pmat_big_df_kernel (writes the split operand blocks)",
                    "post": "post_tcb_kernel + root_tcb_kernel",
-                   "pre": "pre_tcb_a_kernel + pre_tcb_b_kernel + ratio_tc_kernel",
+                   "pre": "pre_tcb_kernel + ratio_tc_kernel",
                    "reduce": "reduce_kernel"}
     phases = {}
     for n_, ms_ in zip(names, phase_ms):

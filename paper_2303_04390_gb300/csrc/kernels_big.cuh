@@ -527,7 +527,9 @@ namespace phylo {
 // cancellation in the sum over eigenvalues.  A CTA computes one 64 x 64
 // tile of P and dP of one (branch, category), streaming the double-float
 // eigenvector tables through shared memory kPmatBigChunk eigenvalues at a
-// time; each thread owns a 4 x 4 block.  For the symmetric decomposition
+// time; each thread owns a 4 x 4 block.  With S_pad 128 (the tensor-core
+// path, whose pre-order step needs no dP) only P is built, written as the
+// split P and P' operand blocks.  For the symmetric decomposition
 // of a reversible model (Vinv[m][t] = pi_t V[t][m]) P - I = K diag(pi) with
 // K = V diag(e) V' symmetric: only the tiles on and above the diagonal are
 // contracted, and an off-diagonal tile also writes its mirror.
@@ -537,6 +539,7 @@ constexpr int kPmatBigChunk = 32;
 template <int SP>
 __global__ void __launch_bounds__(256) pmat_big_df_kernel(PmatArgs a) {
   constexpr int T = SP / 64;
+  constexpr bool kD = SP != 128;  // dP wanted (the S_pad 256 CUDA-core path)
   __shared__ __align__(16) float sv_h[kPmatBigChunk][64], sv_l[kPmatBigChunk][64];
   __shared__ __align__(16) float sw_h[kPmatBigChunk][64], sw_l[kPmatBigChunk][64];
   __shared__ DF se[SP], sd[SP];
@@ -608,11 +611,13 @@ __global__ void __launch_bounds__(256) pmat_big_df_kernel(PmatArgs a) {
       const DF w[4] = {{wh.x, wl.x}, {wh.y, wl.y}, {wh.z, wl.z}, {wh.w, wl.w}};
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const DF ve = df_mul(v[i], em), vd = df_mul(v[i], dm);
+        const DF ve = df_mul(v[i], em);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          df_fma(accP[i][j], ve, w[j]);
-          df_fma(accD[i][j], vd, w[j]);
+        for (int j = 0; j < 4; ++j) df_fma(accP[i][j], ve, w[j]);
+        if constexpr (kD) {
+          const DF vd = df_mul(v[i], dm);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) df_fma(accD[i][j], vd, w[j]);
         }
       }
     }
@@ -621,61 +626,45 @@ __global__ void __launch_bounds__(256) pmat_big_df_kernel(PmatArgs a) {
   const float* pi_h = a.vsplit + 4 * sq;
   const float* pi_l = pi_h + SP;
   if constexpr (SP == 128) {
-    if (a.tiles) {
-      // the tensor-core path's operand blocks instead of P and dP: entry
-      // (s, t) goes to row s % 64, column t % 64 of blocks P (sb, tb) and dP
-      // (sb, tb), and to row t % 64, column s % 64 of block P' (tb, sb); the
-      // mirror entries (t, s) of a reversible model to the transposed places
-      unsigned char* U = static_cast<unsigned char*>(a.tiles) + (size_t)unit * kTcbUnitBytes;
-      float p[4][4], d[4][4];
+    // the tensor-core path's operand blocks instead of P: entry (s, t) goes
+    // to row s % 64, column t % 64 of block P (sb, tb), and to row t % 64,
+    // column s % 64 of block P' (tb, sb); the mirror entries (t, s) of a
+    // reversible model to the transposed places
+    unsigned char* U = static_cast<unsigned char*>(a.tiles) + (size_t)unit * kTcbUnitBytes;
+    float p[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int s = s0 + i, t = t0 + j;
+        DF kp = accP[i][j];
+        if (rev) kp = df_mul(kp, DF{pi_h[t], pi_l[t]});
+        p[i][j] = df_round(kp, s == t && s < S);
+      }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      put_split3_4(U + tcb_block(0, sb, tb), kTerm64, ls + i, lt,
+                   make_float4(p[i][0], p[i][1], p[i][2], p[i][3]));
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      put_split3_4(U + tcb_block(1, tb, sb), kTerm64, lt + j, ls,
+                   make_float4(p[0][j], p[1][j], p[2][j], p[3][j]));
+    if (rev && sb != tb) {  // mirror: P[t][s] = delta + K_st pi_s
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int s = s0 + i, t = t0 + j;
-          DF kp = accP[i][j], kd = accD[i][j];
-          if (rev) {
-            const DF pt = {pi_h[t], pi_l[t]};
-            kp = df_mul(kp, pt);
-            kd = df_mul(kd, pt);
-          }
-          p[i][j] = df_round(kp, s == t && s < S);
-          d[i][j] = df_round(kd, false);
-        }
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        put_split3_4(U + tcb_block(0, sb, tb), kTerm64, ls + i, lt,
-                     make_float4(p[i][0], p[i][1], p[i][2], p[i][3]));
-        put_split3_4(U + tcb_block(1, sb, tb), kTerm64, ls + i, lt,
-                     make_float4(d[i][0], d[i][1], d[i][2], d[i][3]));
-      }
+        for (int j = 0; j < 4; ++j)
+          p[i][j] = df_round(df_mul(accP[i][j], DF{pi_h[s0 + i], pi_l[s0 + i]}), false);
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        put_split3_4(U + tcb_block(2, tb, sb), kTerm64, lt + j, ls,
+        put_split3_4(U + tcb_block(0, tb, sb), kTerm64, lt + j, ls,
                      make_float4(p[0][j], p[1][j], p[2][j], p[3][j]));
-      if (rev && sb != tb) {  // mirror: P[t][s] = delta + K_st pi_s
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const DF ps = {pi_h[s0 + i], pi_l[s0 + i]};
-            p[i][j] = df_round(df_mul(accP[i][j], ps), false);  // = P[t][s]
-            d[i][j] = df_round(df_mul(accD[i][j], ps), false);
-          }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          put_split3_4(U + tcb_block(0, tb, sb), kTerm64, lt + j, ls,
-                       make_float4(p[0][j], p[1][j], p[2][j], p[3][j]));
-          put_split3_4(U + tcb_block(1, tb, sb), kTerm64, lt + j, ls,
-                       make_float4(d[0][j], d[1][j], d[2][j], d[3][j]));
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          put_split3_4(U + tcb_block(2, sb, tb), kTerm64, ls + i, lt,
-                       make_float4(p[i][0], p[i][1], p[i][2], p[i][3]));
-      }
-      return;
+      for (int i = 0; i < 4; ++i)
+        put_split3_4(U + tcb_block(1, sb, tb), kTerm64, ls + i, lt,
+                     make_float4(p[i][0], p[i][1], p[i][2], p[i][3]));
     }
+    return;
   }
   float* P = static_cast<float*>(a.P) + (size_t)unit * sq;
   float* D = static_cast<float*>(a.dP) + (size_t)unit * sq;

@@ -44,7 +44,7 @@ struct Layout {
   Region pattern_w, V, Vinv, lambda, pi, rates, cat_w, t;
   Region vsplit;  // tensor-core path: eigenvectors as double-float tables
   Region tc_tiles;  // 65..128 states, FP32: pre-split matrix blocks
-  Region qt;        // 21..64 states, FP32: Q' as a tensor-core operand
+  Region qt;        // 21..128 states, FP32: Q' as a tensor-core operand
   Region qmat;      // 20 padded states, FP32: Q row-major
   Region tip_desc;  // U-form paths with tip partials: descriptors of the tips
                     // whose U = P p the first post-order launch forms
@@ -119,7 +119,7 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
     ok &= add_region(L, L.post, part);
   }
   ok &= add_region(L, L.pre, part);
-  if (tc) ok &= add_region(L, L.qt, kTcQtBytes);
+  if (tc || uses_tc_big(L.SP, prec == PHYLO_FP64)) ok &= add_region(L, L.qt, qt_bytes(L.SP));
   if (uform && L.SP == 20) ok &= add_region(L, L.qmat, (size_t)L.SP * L.SP * sizeof(float));
   if (C > (1 << 30)) return "n_patterns too large";
   const int planes = escale_planes(L.SP, R, prec == PHYLO_FP64);
@@ -303,6 +303,15 @@ LevelArgs<T> level_args(const phylo_ctx* ctx) {
   a.rates = ctx->dev<double>(ctx->L.rates);
   a.tip_level = 0;
   return a;
+}
+
+// Whether the post-order phase starts with a launch over the tips with
+// partial vectors (the U-form paths form those tips' U first).
+bool has_tip_level(const phylo_ctx* ctx) {
+  if (!ctx->L.tip_desc.bytes) return false;
+  for (int v : ctx->tip_has)
+    if (v) return true;
+  return false;
 }
 
 int* flag_word(const phylo_ctx* ctx) {
@@ -967,8 +976,8 @@ int phylo_set_eigen(phylo_ctx* ctx, const double* V, const double* Vinv,
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }
   if (ctx->L.qt.bytes) {
-    std::vector<unsigned char> qt(kTcQtBytes);
-    build_qt_tile(S, V, Vinv, lambda, qt.data());
+    std::vector<unsigned char> qt(qt_bytes(ctx->L.SP));
+    build_qt_tile(S, ctx->L.SP, V, Vinv, lambda, qt.data());
     if ((rc = upload(ctx, ctx->L.qt, qt.data(), qt.size(), "upload Q operand"))) return rc;
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
   }
@@ -1331,9 +1340,7 @@ int phylo_launches_per_evaluation(const phylo_ctx* ctx) {
     const bool fp64 = ctx->precision == PHYLO_FP64;
     n += (int)(ctx->post_off.size() - 1) + (int)(ctx->pre_off.size() - 1);
     if (uses_tc_terms(ctx->L.SP, fp64)) ++n;  // Eq. 8 ratios
-    // 65..128 states on the tensor cores: two kernels per pre-order level
-    // and Eq. 3 at the root
-    if (uses_tc_big(ctx->L.SP, fp64)) n += (int)(ctx->pre_off.size() - 1) + 1;
+    if (has_tip_level(ctx)) ++n;                // U of the tips with partials
   }
   return n;
 }
@@ -1343,10 +1350,7 @@ int phylo_level_counts(const phylo_ctx* ctx, int* n_post_levels,
   if (!ctx || !n_post_levels || !n_pre_levels) return PHYLO_EINVAL;
   *n_post_levels = ctx->have_tree ? (int)ctx->post_off.size() - 1 : 0;
   *n_pre_levels = ctx->have_tree ? (int)ctx->pre_off.size() - 1 : 0;
-  if (uses_tc_big(ctx->L.SP, ctx->precision == PHYLO_FP64)) {  // see launches_per_evaluation
-    *n_post_levels += *n_post_levels > 0;
-    *n_pre_levels *= 2;
-  }
+  if (ctx->have_tree && ctx->C > 0 && has_tip_level(ctx)) ++*n_post_levels;
   return PHYLO_OK;
 }
 

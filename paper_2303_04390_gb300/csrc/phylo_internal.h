@@ -101,23 +101,32 @@ inline float host_bf16_value(uint16_t b) {
   return f;
 }
 
+// Bytes of the Q' operand for SP = 64 or 128 padded states: (SP / 64)^2
+// blocks of 64 x 64 three-term BF16 values.
+inline size_t qt_bytes(int SP) { return (size_t)(SP / 64) * (SP / 64) * kTcQtBytes; }
+
 // Q' as the three-term BF16 operand of the tensor-core pre-order step (the
 // Eq. 8 numerator through dP = gamma Q P): row s holds column s of
 // Q = V diag(lambda) Vinv (FP64, rounded once to FP32), each FP32 value
 // split as x = t0 + t1 + t2 with t_i the round-to-nearest BF16 of the
-// remainder, stored in the K-major 128-byte-swizzle layout the MMAs read
-// (element (row, k) of a term at row * 128 + (((k / 8) ^ (row % 8)) * 16) +
-// (k % 8) * 2).  Rows and columns past S are zero.  out: kTcQtBytes.
-inline void build_qt_tile(int S, const double* V, const double* Vinv, const double* lambda,
-                          unsigned char* out) {
-  std::memset(out, 0, kTcQtBytes);
+// remainder, cut into 64 x 64 blocks (block (jn, jk) holds rows 64 jn ..,
+// columns 64 jk ..; blocks of one K-block jk adjacent, jn fastest) stored
+// in the K-major 128-byte-swizzle layout the MMAs read (element (row, k) of
+// a term at row * 128 + (((k / 8) ^ (row % 8)) * 16) + (k % 8) * 2, terms
+// 8 KB apart).  Rows and columns past S are zero.  out: qt_bytes(SP).
+inline void build_qt_tile(int S, int SP, const double* V, const double* Vinv,
+                          const double* lambda, unsigned char* out) {
+  std::memset(out, 0, qt_bytes(SP));
   const size_t term = 64 * 128;
+  const int NB = SP / 64;
   for (int s = 0; s < S; ++s)
     for (int t = 0; t < S; ++t) {
       double q = 0.0;  // Q[t][s]
       for (int m = 0; m < S; ++m) q += V[t * S + m] * lambda[m] * Vinv[m * S + s];
       float rem = (float)q;
-      const size_t off = (size_t)s * 128 + ((size_t)((t >> 3) ^ (s & 7)) << 4) + (t & 7) * 2;
+      const int n = s & 63, k = t & 63;
+      const size_t blk = ((size_t)(t >> 6) * NB + (s >> 6)) * kTcQtBytes;
+      const size_t off = blk + (size_t)n * 128 + ((size_t)((k >> 3) ^ (n & 7)) << 4) + (k & 7) * 2;
       for (int i = 0; i < 3; ++i) {
         const uint16_t b = host_bf16(rem);
         std::memcpy(out + i * term + off, &b, 2);
@@ -127,10 +136,13 @@ inline void build_qt_tile(int S, const double* V, const double* Vinv, const doub
 }
 
 // FP32 paths whose post-order pass stores U = P p per node instead of p
-// (20 padded states, kernels.cuh; 21..64 states, kernels_tc64.cuh): tips
+// (20 padded states, kernels.cuh; 21..64 and 65..128 states, kernels_tc64.cuh
+// and kernels_tcb.cuh): tips
 // with partial vectors keep their U in extra slots of the post region, and
 // the pre-order step forms Eq. 8's numerator through Q.
-inline bool uses_u_form(int SP, bool fp64) { return (SP == 20 || SP == 64) && !fp64; }
+inline bool uses_u_form(int SP, bool fp64) {
+  return (SP == 20 || SP == 64 || SP == 128) && !fp64;
+}
 
 // Q = V diag(lambda) Vinv in FP64, rounded once to FP32, row-major SP x SP
 // with zero padding (the 20-state U form's pre-order step).
@@ -147,12 +159,12 @@ inline void build_q_matrix(int S, int SP, const double* V, const double* Vinv,
 
 // FP32 with 65..128 states runs on the tensor cores too (kernels_tcb.cuh):
 // 128-pattern tiles, per-category exponents, and the matrices written by
-// the matrix kernel directly as 64 x 64 BF16 operand blocks (kind P, dP, P'
+// the matrix kernel directly as 64 x 64 BF16 operand blocks (kind P, P'
 // x 2 x 2 blocks of 24 KB per (branch, category)).
 inline bool uses_tc_big(int SP, bool fp64) { return SP == 128 && !fp64; }
-constexpr size_t kTcbUnitBytes = 3 * 2 * 2 * (3 * 64 * 128);
+constexpr size_t kTcbUnitBytes = 2 * 2 * 2 * (3 * 64 * 128);
 // Offset of block (kind, jn, jk) in a (branch, category) unit: kind 0 = P,
-// 1 = dP, 2 = P' (its rows are the columns of P); block row n, column k
+// 1 = P' (its rows are the columns of P); block row n, column k
 // holds M[64 jn + n][64 jk + k] as three BF16 terms of 8 KB each, in the
 // K-major 128-byte-swizzle layout of tc.cuh.  The blocks of one K-block jk
 // are adjacent (jn fastest), so one bulk copy stages a contraction round.

@@ -327,7 +327,7 @@ int phylo_evaluate_noalloc(int N, int C, int S, int R, const int32_t* parent,
   }
   static thread_local unsigned char qt[kTcQtBytes];
   if (L.qt.bytes) {
-    build_qt_tile(S, V, Vinv, lambda, qt);
+    build_qt_tile(S, L.SP, V, Vinv, lambda, qt);
     NA_TRY(up(L.qt, qt, kTcQtBytes), "upload Q operand");
   }
   NA_TRY(up(L.lambda, lambda, (size_t)S * 8), "upload lambda");
