@@ -14,8 +14,8 @@ patterns or inside a pattern (|g*| << B) cannot be held to a bound relative
 to |g*| by any finite-precision evaluation -- two FP64 evaluations in
 different but exact orders already differ by ~1e-14 B -- so the bound falls
 back to a fraction of B.  FP32: the measured worst on the full-size
-workloads is 4.6e-7 B (codon-128; hky-1024 1.5e-7 B, aa-256 and mmm-122
-4e-8 B).  FP64: the eigen route of Eq. 1
+workloads is 4.1e-7 B (codon-128; mmm-122 3.6e-7 B, hky-1024 1.5e-7 B,
+aa-256 4e-8 B).  FP64: the eigen route of Eq. 1
 leaves an absolute error of order S u sqrt(pi_max / pi_min) in the small
 entries of P (two- and three-nucleotide codon changes on short branches),
 which the 61-state workload turns into ~3e-12 B; the Taylor route of the

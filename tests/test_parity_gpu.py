@@ -72,6 +72,13 @@ SMALL = [
     (5, 65, 8, 21, "yule"),            # smallest S of S_pad 128, eight categories
     (4, 129, 3, 18, "balanced"),       # smallest S of S_pad 256
     (30, 122, 2, 17, "caterpillar"),   # deep chain at 122 states: rescaling at every node
+    # the U form (FP32, 5-128 states): two-taxon trees (the root level alone)
+    # and the largest and smallest state counts of each padded size
+    (2, 20, 4, 9, "yule"),
+    (2, 61, 2, 130, "yule"),
+    (2, 122, 1, 7, "yule"),
+    (3, 21, 4, 129, "caterpillar"),
+    (4, 128, 2, 40, "balanced"),
 ]
 
 
@@ -101,6 +108,22 @@ def test_tip_partials(S, precision):
     ref = oracle_eval(w, tip_partials=tp)
     _, logL, grad = _gpu(w, precision, tip_partials=tp)
     compare(logL, grad, ref, precision, "tip partials")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("S", [20, 61, 122])
+def test_tip_partials_two_taxa(S, precision):
+    """Both tips of a two-taxon tree carry partial vectors: the U form's
+    first post-order launch (the tips' U) feeds the root level directly."""
+    w = synth.small_workload(2, S, 4, 33, seed=31)
+    from oracle import phylo_oracle as O
+    tp = O.tip_partial_vectors(S, w.tip_states)
+    rng = np.random.default_rng(S + 1)
+    for tip in [0, 1]:
+        tp[tip] = rng.random((33, S)) ** 3 + 0.01
+    ref = oracle_eval(w, tip_partials=tp)
+    _, logL, grad = _gpu(w, precision, tip_partials=tp)
+    compare(logL, grad, ref, precision, "tip partials, two taxa")
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
