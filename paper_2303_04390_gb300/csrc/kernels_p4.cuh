@@ -20,6 +20,14 @@
 //    so each warp's access of one category is 512 contiguous bytes;
 //  - a tile's (warp's) gradient sums are FP32 pairs kept exact with
 //    error-free transformations (converted to FP64 by the final reduction).
+// The U form: the post-order step of a (non-cherry, non-root) node k stores
+// U_k = P_k p_k, the factor k contributes to its parent in Eq. 2, instead of
+// p_k, so its parent reads U_k where it read p_k (the same bytes) and skips
+// that product; in the pre-order step such a child's Eq. 8 numerator is
+// gamma_r (a' Q) U (q' Q p with q = P' a, P = exp(gamma_r t Q) commuting
+// with Q): one product where P p and dP p were two.  Cherries, tips with
+// partial vectors and compact tips keep the p form (their U, dP p or
+// columns are formed from the tip data in the step that needs them).
 #pragma once
 
 namespace phylo {
@@ -71,11 +79,14 @@ __device__ __forceinline__ float max4(float2 lo, float2 hi) {
 // Shared layout of one block.  m[x] holds child x's branch block as the
 // matrix kernel wrote it: P' of every category (R x 16 floats) and, for the
 // pre-order step, dP' and P after it (float4 offsets 0, 4R and 8R).  g holds
-// P' of the tip branches below a cherry child (i: 0, 1; j: 2, 3).
+// P' of the tip branches below a cherry child (i: 0, 1; j: 2, 3).  n holds
+// the node's own P' (post-order: U_k = P_k p_k) or Q (pre-order, one
+// matrix: the Eq. 8 numerator of a child whose U is stored).
 template <int RM, bool PRE, bool CH>
 struct P4Mats {
   float4 m[2][(PRE ? kP4MatKinds : 1) * RM * 4];
   float4 g[CH ? 4 : 1][RM * 4];
+  float4 n[PRE ? 4 : RM * 4];
 };
 
 // Power-of-two rescale of a vector whose largest magnitude is mx (finite,
@@ -129,11 +140,16 @@ __device__ __forceinline__ void p4_child(int y, int S, float4 v,
   if (WITH_D) mv4t(DT, v, wlo, whi);
 }
 
-// The pre-order kernel is latency-bound at these occupancies: asking for 12
-// resident blocks per SM (at most 85 registers a thread) measured 4% faster
-// than the unbounded register allocation; the post-order kernel is left
-// unbounded.
-constexpr int kP4PreMinBlocks = 12;
+// The pre-order kernel is latency-bound at these occupancies: in the p form
+// asking for 12 resident blocks per SM (at most 85 registers a thread)
+// measured 4% faster than the unbounded register allocation; in the U form
+// that bound spills and 11 blocks (at most 88 registers) measured best
+// (hky-1024 pre-order 0.434 ms; 12 blocks 0.444, 10 blocks 0.467).  The
+// post-order kernel is left unbounded.
+#ifndef PHYLO_P4_PRE_BLOCKS
+#define PHYLO_P4_PRE_BLOCKS 11
+#endif
+constexpr int kP4PreMinBlocks = PHYLO_P4_PRE_BLOCKS;
 
 // RM: categories unrolled (R <= RM); EX: R == RM, so that no per-category
 // test is left at run time.
@@ -161,9 +177,12 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
   pdl_wait_and_release();
   if (tid == 0) {
     const int n_ch = (int)hi_ + (int)hj_;
-    mbar_expect_tx(&bar, 2 * cbytes + 2 * n_ch * mbytes);
+    // the node's own P' (post-order, not at the root) or Q (pre-order)
+    const uint32_t nbytes = PRE ? 64u : (k != a.root ? mbytes : 0u);
+    mbar_expect_tx(&bar, 2 * cbytes + 2 * n_ch * mbytes + nbytes);
     bulk_g2s(sm.m[0], a.P + (size_t)bi * bstride, cbytes, &bar);
     bulk_g2s(sm.m[1], a.P + (size_t)bj * bstride, cbytes, &bar);
+    if (nbytes) bulk_g2s(sm.n, PRE ? a.qmat : a.P + (size_t)k * bstride, nbytes, &bar);
     if constexpr (CH) {
       for (int x = 0; x < 2; ++x) {
         if (!(x == 0 ? hi_ : hj_)) continue;
@@ -243,8 +262,10 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       }
     }
   }
+  // children whose U = P p is stored (non-cherry internal nodes)
+  const bool su_i = bi >= a.n_tips && !hi_, su_j = bj >= a.n_tips && !hj_;
   if (!PRE) {
-    // ---- Eq. 2: p_k = (P_i p_i) o (P_j p_j) for every category ------------
+    // ---- Eq. 2: p_k = U_i o U_j for every category -------------------------
     float2 plo[RM], phi[RM];
     float m = 0.f;
 #pragma unroll
@@ -252,8 +273,10 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       plo[r] = make_float2(0.f, 0.f); phi[r] = plo[r];
       if (r < R) {
         float2 ilo, ihi, jlo, jhi, d0, d1;
-        p4_child<false>(yi, S, vi[r], PTi + r * 4, nullptr, ilo, ihi, d0, d1);
-        p4_child<false>(yj, S, vj[r], PTj + r * 4, nullptr, jlo, jhi, d0, d1);
+        if (su_i) { ilo = lo2(vi[r]); ihi = hi2(vi[r]); }
+        else p4_child<false>(yi, S, vi[r], PTi + r * 4, nullptr, ilo, ihi, d0, d1);
+        if (su_j) { jlo = lo2(vj[r]); jhi = hi2(vj[r]); }
+        else p4_child<false>(yj, S, vj[r], PTj + r * 4, nullptr, jlo, jhi, d0, d1);
         plo[r] = __fmul2_rn(ilo, jlo);
         phi[r] = __fmul2_rn(ihi, jhi);
         m = fmaxf(m, max4(plo[r], phi[r]));
@@ -267,14 +290,16 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     }
     e += ei + ej;
     if (k != a.root) {
-      if (valid) {
+      if (valid) {  // U_k = P_k p_k, stored with p_k's exponent
         float4* out = reinterpret_cast<float4*>(a.post) + p4_index(k - a.n_tips, c, 0, R, a.n_tiles);
 #pragma unroll
         for (int r = 0; r < RM; ++r)
           if (r < R) {
             const float2 lo = __fmul2_rn(plo[r], make_float2(f, f));
             const float2 hi = __fmul2_rn(phi[r], make_float2(f, f));
-            out[32 * r] = make_float4(lo.x, lo.y, hi.x, hi.y);
+            float2 ulo, uhi;
+            mv4t(sm.n + r * 4, make_float4(lo.x, lo.y, hi.x, hi.y), ulo, uhi);
+            out[32 * r] = make_float4(ulo.x, ulo.y, uhi.x, uhi.y);
           }
         a.escale[(size_t)(k - a.n_tips) * a.escale_stride + c] = e;
       }
@@ -307,13 +332,31 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
     if (r < R) {
       const float2 ql = lo2(q[r]), qh = hi2(q[r]);
       float2 uilo, uihi, wilo, wihi, ujlo, ujhi, wjlo, wjhi;
-      p4_child<true>(yi, S, vi[r], PTi + r * 4, DTi + r * 4, uilo, uihi, wilo, wihi);
-      p4_child<true>(yj, S, vj[r], PTj + r * 4, DTj + r * 4, ujlo, ujhi, wjlo, wjhi);
+      // a stored U needs no product here; the others give U and dP p (or columns)
+      if (su_i) { uilo = lo2(vi[r]); uihi = hi2(vi[r]); }
+      else p4_child<true>(yi, S, vi[r], PTi + r * 4, DTi + r * 4, uilo, uihi, wilo, wihi);
+      if (su_j) { ujlo = lo2(vj[r]); ujhi = hi2(vj[r]); }
+      else p4_child<true>(yj, S, vj[r], PTj + r * 4, DTj + r * 4, ujlo, ujhi, wjlo, wjhi);
       const float2 ailo = __fmul2_rn(ql, ujlo), aihi = __fmul2_rn(qh, ujhi);  // a_i
       const float2 ajlo = __fmul2_rn(ql, uilo), ajhi = __fmul2_rn(qh, uihi);  // a_j
       const float w = a.cat_wt[r];
-      Ni = fmaf(w, dot22(ailo, aihi, wilo, wihi), Ni);
-      Nj = fmaf(w, dot22(ajlo, ajhi, wjlo, wjhi), Nj);
+      float ni, nj;
+      if (su_i || su_j) {
+        const float gam = (float)a.rates[r];
+        float2 lo, hi;
+        if (su_i) {  // gamma_r (a_i' Q) U_i
+          mtv4r(sm.n, ailo, aihi, lo, hi);
+          ni = gam * dot22(lo, hi, uilo, uihi);
+        }
+        if (su_j) {
+          mtv4r(sm.n, ajlo, ajhi, lo, hi);
+          nj = gam * dot22(lo, hi, ujlo, ujhi);
+        }
+      }
+      if (!su_i) ni = dot22(ailo, aihi, wilo, wihi);
+      if (!su_j) nj = dot22(ajlo, ajhi, wjlo, wjhi);
+      Ni = fmaf(w, ni, Ni);
+      Nj = fmaf(w, nj, Nj);
       Dn = fmaf(w, dot22(ailo, aihi, uilo, uihi), Dn);
       if (int_i) {
         mtv4r(Pi + r * 4, ailo, aihi, qilo[r], qihi[r]);

@@ -45,7 +45,7 @@ struct Layout {
   Region vsplit;  // tensor-core path: eigenvectors as double-float tables
   Region tc_tiles;  // 65..128 states, FP32: pre-split matrix blocks
   Region qt;        // 21..128 states, FP32: Q' as a tensor-core operand
-  Region qmat;      // 20 padded states, FP32: Q row-major
+  Region qmat;      // 4 and 20 padded states, FP32: Q row-major
   Region tip_desc;  // U-form paths with tip partials: descriptors of the tips
                     // whose U = P p the first post-order launch forms
   Region pattern_wt, cat_wt, pi_t;  // weights and pi in the path's type
@@ -120,7 +120,8 @@ const char* compute_layout(int N, int C, int S, int R, int prec, int flags,
   }
   ok &= add_region(L, L.pre, part);
   if (tc || uses_tc_big(L.SP, prec == PHYLO_FP64)) ok &= add_region(L, L.qt, qt_bytes(L.SP));
-  if (uform && L.SP == 20) ok &= add_region(L, L.qmat, (size_t)L.SP * L.SP * sizeof(float));
+  if (prec == PHYLO_FP32 && (L.SP == 4 || L.SP == 20))  // the U form's Q (FP32, row-major)
+    ok &= add_region(L, L.qmat, (size_t)L.SP * L.SP * sizeof(float));
   if (C > (1 << 30)) return "n_patterns too large";
   const int planes = escale_planes(L.SP, R, prec == PHYLO_FP64);
   if (!mul_ok(n_int * planes, (size_t)round_up(C, 4) * sizeof(int), &tmp))

@@ -145,7 +145,7 @@ inline bool uses_u_form(int SP, bool fp64) {
 }
 
 // Q = V diag(lambda) Vinv in FP64, rounded once to FP32, row-major SP x SP
-// with zero padding (the 20-state U form's pre-order step).
+// with zero padding (the pre-order step of the 4- and 20-state U form).
 inline void build_q_matrix(int S, int SP, const double* V, const double* Vinv,
                            const double* lambda, float* out) {
   for (int i = 0; i < SP * SP; ++i) out[i] = 0.f;
@@ -286,7 +286,7 @@ struct LevelArgs {
   const unsigned char* tc_tiles;  // 65..128 states, FP32: the pre-split matrix
                                   // blocks [2N-2][R][kTcbUnitBytes] (else null)
   const unsigned char* qt;     // 21..64 states, FP32: Q' operand (kTcQtBytes)
-  const float* qmat;           // 20 padded states, FP32: Q row-major [20][20]
+  const float* qmat;           // 4 and 20 padded states, FP32: Q row-major [SP][SP]
   const double* rates;         // [R] category rates gamma_r
   int tip_level;               // U-form paths: the level's nodes are tips with
                                // partials (their U = P p, before level 1)

@@ -100,7 +100,7 @@ void na_layout(int N, int C, int S, int R, NaLayout* Lp) {
     na_add(L, L.rterm, n_int * (size_t)C * R * 16);
     na_add(L, L.qt, kTcQtBytes);
   }
-  if (L.SP == 20) na_add(L, L.qmat, (size_t)L.SP * L.SP * sizeof(float));
+  if (L.SP == 4 || L.SP == 20) na_add(L, L.qmat, (size_t)L.SP * L.SP * sizeof(float));
   na_add(L, L.tip_states, (size_t)N * tip_state_stride(C));
   na_add(L, L.pattern_w, (size_t)C * 8);
   na_add(L, L.V, (size_t)S * S * 8);
