@@ -29,8 +29,8 @@
  *  - Matrices are row-major FP64.  Sizes: N tips, C patterns, S states
  *    (2 <= S <= 256; S <= 64 for phylo_evaluate_noalloc), R categories
  *    (1 <= R <= 8).  Kernels by padded state count S_pad: 4 and 20 (CUDA
- *    cores), 64 (FP32: tensor cores), 128 and 256 (CUDA cores, matrices
- *    streamed through shared memory).
+ *    cores), 64 and 128 (FP32: tensor cores), 256 and the FP64 path above 64
+ *    (CUDA cores, matrices streamed through shared memory).
  */
 #ifndef PHYLO_API_H
 #define PHYLO_API_H
