@@ -59,6 +59,29 @@ def test_workspace_bytes(lib):
     assert tp - workspace_bytes(16, 100, 20, 4, "fp32") >= 16 * 100 * 20 * 4
 
 
+@pytest.mark.parametrize("S, SP, per_tip", [(20, 20, None), (61, 64, None), (122, 128, None),
+                                            (4, 4, 0), (61, 64, 0)])
+def test_workspace_u_slots_for_tip_partials(lib, S, SP, per_tip):
+    """The U-form FP32 paths (20, 64 and 128 padded states) keep U = P p of
+    every tip with partials in N extra post-order slots ([C][R][S_pad] FP32
+    each, tile-padded for 20 states) beside the tips' partials ([C][S_pad]);
+    the 4-state path and the FP64 path form a tip's product where it is
+    needed and only store the partials."""
+    from paper_2303_04390_gb300 import workspace_bytes
+    N, C, R = 16, 100, 4
+    prec = "fp32" if per_tip is None else ("fp32" if SP == 4 else "fp64")
+    grow = (workspace_bytes(N, C, S, R, prec, tip_partials=True)
+            - workspace_bytes(N, C, S, R, prec))
+    elem = 4 if prec == "fp32" else 8
+    partials = N * C * SP * elem
+    if per_tip is None:  # tip partials plus N U slots
+        slots = N * C * R * SP * 4
+        assert grow >= partials + slots
+        assert grow < partials + 2 * slots + 65536
+    else:                # tip partials only
+        assert partials <= grow < partials + 65536
+
+
 @pytest.mark.parametrize("args", [(1, 10, 4, 1), (8, -1, 4, 1), (8, 10, 1, 1),
                                   (8, 10, 257, 1), (8, 10, 4, 0), (8, 10, 4, 9),
                                   (70000, 10, 4, 1)])

@@ -126,6 +126,26 @@ def test_tip_partials_two_taxa(S, precision):
     compare(logL, grad, ref, precision, "tip partials, two taxa")
 
 
+@pytest.mark.parametrize("S", [20, 61, 122])
+def test_tip_level_launch(S):
+    """On the U-form FP32 paths a tip with partials adds one post-order
+    launch (its U = P p, formed before the first level); the result still
+    matches the oracle."""
+    import paper_2303_04390_gb300 as pg
+    w = synth.small_workload(9, S, 2, 40, seed=33)
+    plain = pg.from_workload(w, "fp32")
+    n0, (p0, q0) = plain.launches_per_evaluation(), plain.level_counts()
+    plain.close()
+    from oracle import phylo_oracle as O
+    tp = O.tip_partial_vectors(S, w.tip_states)
+    tp[4] = np.random.default_rng(S).random((40, S)) + 0.05
+    ctx, logL, grad = _gpu(w, "fp32", tip_partials=tp)
+    assert ctx.launches_per_evaluation() == n0 + 1
+    assert ctx.level_counts() == (p0 + 1, q0)
+    ctx.close()
+    compare(logL, grad, oracle_eval(w, tip_partials=tp), "fp32", "tip level")
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("S", [4, 61, 122])
 def test_zero_length_branches(S, precision):
