@@ -735,6 +735,31 @@ __device__ __forceinline__ void u20_resolve(const ChildIn<float, kU20>& in, int 
 #define PHYLO_U20_PRE_BLOCKS 4
 #endif
 
+// Post-order staging (thread 0): only what a lookup or U_k reads, P' of
+// compact-tip children (a stored child's U is already P p) and of the node
+// unless it is the root.
+template <int RP, int NPT>
+__device__ __forceinline__ void post_u20_stage(const LevelArgs<float>& a, const int4 (&d)[NPT],
+                                               int nn, bool tip, float* mats, uint64_t* bar) {
+  constexpr int SP = kU20, MS = MatStride<float, SP>::v;
+  if (threadIdx.x != 0) return;
+  uint32_t nmat = 0;
+  for (int u = 0; u < nn; ++u)
+    nmat += (!tip && (d[u].w & kDescCompactX)) + (!tip && (d[u].w & kDescCompactY)) +
+            (d[u].x != a.root);
+  mbar_expect_tx(bar, nmat * (uint32_t)(a.n_cat * SP * SP * sizeof(float)));
+  for (int u = 0; u < nn; ++u) {
+    float* slots = mats + (size_t)(3 * u) * RP * MS;
+    const int br[3] = {d[u].y, d[u].z, d[u].x};
+    const bool need[3] = {!tip && (d[u].w & kDescCompactX), !tip && (d[u].w & kDescCompactY),
+                          d[u].x != a.root};
+    for (int x = 0; x < 3; ++x)
+      if (need[x])
+        issue_mats<float, SP, RP>(a.P, br + x, 1, a.n_cat, slots + (size_t)x * RP * MS, bar,
+                                  kP4MatKinds, 0);
+  }
+}
+
 // Post-order level: per node of the block, slots [P'_child0 | P'_child1 |
 // P'_node] (every category); on the tip level, P'_tip alone.
 template <int RP, int NPT>
@@ -758,24 +783,13 @@ post_u20_kernel(LevelArgs<float> a) {
   const bool tip = a.tip_level;
   if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
   __syncthreads();
-  pdl_wait_and_release();
-  int4 d[NPT];
+  int4 d[NPT];  // host-written: readable before the wait
 #pragma unroll
   for (int u = 0; u < NPT; ++u)
     d[u] = u < nn ? a.level_desc[g0 + u] : make_int4(0, 0, 0, 0);
-  if (threadIdx.x == 0) {
-    uint32_t nmat = 0;
-    for (int u = 0; u < nn; ++u) nmat += tip ? 1 : (d[u].x == a.root ? 2 : 3);
-    mbar_expect_tx(&bar, nmat * (uint32_t)(R * SP * SP * sizeof(float)));
-    for (int u = 0; u < nn; ++u) {
-      float* slots = mats + (size_t)(3 * u) * RP * MS;
-      const int br[3] = {d[u].y, d[u].z, d[u].x};
-      for (int x = tip ? 2 : 0; x < 3; ++x)
-        if (x < 2 || d[u].x != a.root)
-          issue_mats<float, SP, RP>(a.P, br + x, 1, R, slots + (size_t)x * RP * MS, &bar,
-                                    kP4MatKinds, 0);
-    }
-  }
+  if (a.mats_ready) post_u20_stage<RP, NPT>(a, d, nn, tip, mats, &bar);
+  pdl_wait_and_release();
+  if (!a.mats_ready) post_u20_stage<RP, NPT>(a, d, nn, tip, mats, &bar);
   ChildIn<float, SP> in[NPT][2];
 #pragma unroll
   for (int u = 0; u < NPT; ++u) {
@@ -840,6 +854,35 @@ post_u20_kernel(LevelArgs<float> a) {
   }
 }
 
+// Pre-order staging (thread 0): Q (host-written) and only what the node's
+// children read, P' and dP' of a compact tip (its U and numerator are
+// lookups) and P of an internal child (q_x = P' a_x); a tip with partials
+// needs neither.
+template <int RP, int NPT>
+__device__ __forceinline__ void pre_u20_stage(const LevelArgs<float>& a, const int4 (&d)[NPT],
+                                              int nn, float* mats, float* Qm, uint64_t* bar) {
+  constexpr int SP = kU20, MS = MatStride<float, SP>::v, NS = 6;
+  if (threadIdx.x != 0) return;
+  const int fl[2] = {kDescCompactX, kDescCompactY};
+  uint32_t nmat = 0;
+  for (int u = 0; u < nn; ++u) {
+    const int br[2] = {d[u].y, d[u].z};
+    for (int x = 0; x < 2; ++x) nmat += (d[u].w & fl[x]) ? 2 : (br[x] >= a.n_tips);
+  }
+  mbar_expect_tx(bar, (uint32_t)((nmat * a.n_cat + 1) * SP * SP * sizeof(float)));
+  bulk_g2s(Qm, a.qmat, (uint32_t)(SP * SP * sizeof(float)), bar);
+  for (int u = 0; u < nn; ++u) {
+    const int br[2] = {d[u].y, d[u].z};
+    float* slots = mats + (size_t)(NS * u) * RP * MS;
+    for (int x = 0; x < 2; ++x)
+      for (int kind = 0; kind < kP4MatKinds; ++kind)
+        if ((d[u].w & fl[x]) ? kind < 2 : (kind == 2 && br[x] >= a.n_tips))
+          issue_mats<float, SP, RP>(a.P, br + x, 1, a.n_cat,
+                                    slots + (size_t)(2 * kind + x) * RP * MS, bar, kP4MatKinds,
+                                    kind);
+  }
+}
+
 // Pre-order level with the fused gradient: slots per node [P'_i | P'_j |
 // dP'_i | dP'_j | P_i | P_j] (every category), then Q (one matrix).
 template <int RP, int NPT>
@@ -864,22 +907,13 @@ pre_u20_kernel(LevelArgs<float> a) {
   const int rr = r < R ? r : 0;
   if (threadIdx.x == 0) mbar_init_fenced(&bar, 1);
   __syncthreads();
-  pdl_wait_and_release();
-  int4 d[NPT];
+  int4 d[NPT];  // host-written: readable before the wait
 #pragma unroll
   for (int u = 0; u < NPT; ++u)
     d[u] = u < nn ? a.level_desc[g0 + u] : make_int4(0, 0, 0, 0);
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar, (uint32_t)((NS * nn * R + 1) * SP * SP * sizeof(float)));
-    bulk_g2s(Qm, a.qmat, (uint32_t)(SP * SP * sizeof(float)), &bar);
-    for (int u = 0; u < nn; ++u) {
-      const int br[2] = {d[u].y, d[u].z};
-      float* slots = mats + (size_t)(NS * u) * RP * MS;
-      for (int kind = 0; kind < kP4MatKinds; ++kind)
-        issue_mats<float, SP, RP>(a.P, br, 2, R, slots + (size_t)(2 * kind) * RP * MS, &bar,
-                                  kP4MatKinds, kind);
-    }
-  }
+  if (a.mats_ready) pre_u20_stage<RP, NPT>(a, d, nn, mats, Qm, &bar);
+  pdl_wait_and_release();
+  if (!a.mats_ready) pre_u20_stage<RP, NPT>(a, d, nn, mats, Qm, &bar);
   float q[NPT][SP];
   ChildIn<float, SP> in[NPT][2];
 #pragma unroll

@@ -174,8 +174,11 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
   const size_t bstride = (size_t)kP4MatKinds * R * 16;      // floats per branch
   if (tid == 0) mbar_init_fenced(&bar, 1);
   __syncthreads();
-  pdl_wait_and_release();
-  if (tid == 0) {
+  // The descriptor, the tree and the tip states are written by the host and
+  // read before the wait; so are the matrices when the launch before this
+  // one is not the matrix kernel.
+  auto issue_copies = [&] {
+    if (tid != 0) return;
     const int n_ch = (int)hi_ + (int)hj_;
     // the node's own P' (post-order, not at the root) or Q (pre-order)
     const uint32_t nbytes = PRE ? 64u : (k != a.root ? mbytes : 0u);
@@ -191,7 +194,8 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
         bulk_g2s(sm.g[2 * x + 1], a.P + (size_t)g.y * bstride, mbytes, &bar);
       }
     }
-  }
+  };
+  if (a.mats_ready) issue_copies();
   // ---- every global load of this pattern, issued before any use ----------
   float4 vi[RM], vj[RM], q[RM];
   int yi = -1, yj = -1, ei = 0, ej = 0;
@@ -209,6 +213,8 @@ __global__ void __launch_bounds__(kP4Threads, PRE ? kP4PreMinBlocks : 0)
       yb[1] = a.tip_states[(size_t)gj2.y * a.state_stride + c];
     }
   }
+  pdl_wait_and_release();
+  if (!a.mats_ready) issue_copies();
 #pragma unroll
   for (int r = 0; r < RM; ++r) {
     const bool on = valid && r < R;

@@ -529,7 +529,6 @@ __device__ __forceinline__ int rescale_exponent(float m, bool valid, int* err) {
 template <typename T>  // float only
 __global__ void __launch_bounds__(kTcThreads, PHYLO_POST_U_BLOCKS) post_u_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
-  pdl_wait_and_release();  // before TMEM, smem or any global access
   static_assert(kStageBytes <= kOp128, "staging fits in the operand buffer");
   static_assert(2 * kPt32Bytes <= kOp128, "staged lookup tables fit in the operand buffer");
   extern __shared__ unsigned char smraw[];
@@ -551,7 +550,10 @@ __global__ void __launch_bounds__(kTcThreads, PHYLO_POST_U_BLOCKS) post_u_kernel
   const bool tip = a.tip_level;
   const TcChild xs[2] = {tc_child(a.n_tips, d.y, d.w & kDescFlagCompact0),
                          tc_child(a.n_tips, d.z, d.w & kDescFlagCompact1)};
-  if (tid == 0) {
+  // The descriptor (host-written) is read before the wait; so are the
+  // matrix tiles when the launch before this one is not the matrix kernel.
+  auto issue_operands = [&] {
+    if (tid != 0) return;
     mbar_init_fenced(&bar_tma, 1);
     mbar_init_fenced(&bar_mma, 1);
     uint32_t bytes = kOp64;
@@ -564,7 +566,10 @@ __global__ void __launch_bounds__(kTcThreads, PHYLO_POST_U_BLOCKS) post_u_kernel
         if (xs[x].compact)
           bulk_g2s(A + x * kPt32Bytes, unit_tiles(a, xs[x].b, r) + kUnitPt32, kPt32Bytes,
                    &bar_tma);
-  }
+  };
+  if (a.mats_ready) issue_operands();
+  pdl_wait_and_release();  // before TMEM or any other global access
+  if (!a.mats_ready) issue_operands();
   // every global load is issued before the first wait
   UFetch f0, f1;
   if (tip) {
@@ -715,7 +720,6 @@ __global__ void __launch_bounds__(kTcRows) root_u_kernel(LevelArgs<T> a) {
 template <typename T>  // float only
 __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
   static_assert(std::is_same<T, float>::value, "tensor-core path is FP32");
-  pdl_wait_and_release();  // before TMEM, smem or any global access
   static_assert(kStageBytes <= kOp128 && kStageBytes <= 2 * kOp64, "staging fits");
   static_assert(kPt32Bytes <= kOp64, "a lookup table fits in the P' buffer");
   extern __shared__ unsigned char smraw[];
@@ -745,7 +749,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
   const size_t kslot = (size_t)(k - a.n_tips);
   const int c0 = blockIdx.x * kTcRows;
   const int estr = a.escale_stride;
-  if (tid == 0) {
+  // The descriptor, Q' and the category constants (all written before the
+  // matrix kernel ran) are read before the wait; so are the matrix tiles
+  // when the launch before this one is not the matrix kernel.
+  auto issue_operands = [&] {
+    if (tid != 0) return;
     mbar_init_fenced(&bar_tma, 1);
     mbar_init_fenced(&bar_mma, 1);
     mbar_expect_tx(&bar_tma, kOp64 + (cx.internal ? kOp64 : 0) +
@@ -756,10 +764,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) pre_u_kernel(LevelArgs<T> a) {
       bulk_g2s(Bp, unit_tiles(a, cx.b, r) + kUnitPt32, kPt32Bytes, &bar_tma);
     if (cy.compact)
       bulk_g2s(A, unit_tiles(a, cy.b, r) + kUnitPt32, kPt32Bytes, &bar_tma);
-  }
-  // every global load is issued before the first wait
+  };
   const double cw = a.cat_w[r], rate = a.rates[r];  // used in the epilogue
   const float wr = a.cat_wt[r];
+  if (a.mats_ready) issue_operands();
+  pdl_wait_and_release();  // before TMEM or any other global access
+  if (!a.mats_ready) issue_operands();
+  // every global load is issued before the first wait
   float4 q[8];
   int eq[4];
   if (!root) {

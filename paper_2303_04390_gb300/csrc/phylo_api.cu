@@ -367,12 +367,18 @@ cudaError_t enqueue_phase(phylo_ctx* ctx, int phase, cudaStream_t st) {
       at.root_level = 0;
       at.level_cherry = 0;
       at.tip_level = 1;
+      at.mats_ready = 0;  // directly after the matrix kernel
       e = launch_post_level<T>(at, ctx->L.SP, ctx->L.RP, st);
       if (e != cudaSuccess) return e;
     }
+    // P may be staged before the wait on the previous launch unless that
+    // launch is the matrix kernel itself (the first post-order launch).
+    bool after_pmat = post && !(ctx->L.tip_desc.bytes && a.tip_partials);
     for (size_t l = 0; l + 1 < off.size(); ++l) {
       NvtxRange range(post ? "phylo post-order level (Eq. 2)"
                            : "phylo pre-order level (Eqs. 4, 8)", (int)l);
+      a.mats_ready = after_pmat ? 0 : 1;
+      after_pmat = false;
       a.level_nodes = nodes + off[l];
       a.level_desc = desc + off[l];
       a.n_level = off[l + 1] - off[l];

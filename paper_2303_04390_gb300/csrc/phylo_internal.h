@@ -290,6 +290,10 @@ struct LevelArgs {
   const double* rates;         // [R] category rates gamma_r
   int tip_level;               // U-form paths: the level's nodes are tips with
                                // partials (their U = P p, before level 1)
+  int mats_ready;              // 1 if P was complete before the previous launch
+                               // began (every launch but the first after the
+                               // matrix kernel): the level may read P and its
+                               // descriptors before griddepcontrol.wait
 };
 
 struct PmatArgs {

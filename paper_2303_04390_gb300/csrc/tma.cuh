@@ -81,7 +81,10 @@ __device__ __forceinline__ void cp_async_wait() {
 // Programmatic dependent launch: wait until the kernel before this one in
 // the stream has completed with its writes visible, then let the kernel
 // after this one start launching its CTAs (they wait the same way before
-// touching memory).  Without the launch attribute both are no-ops.
+// touching memory).  Without the launch attribute both are no-ops.  Since
+// every kernel waits before it releases, a kernel that has started can only
+// overlap the one directly before it: everything launched earlier has
+// completed, so data those kernels wrote may be read before the wait.
 __device__ __forceinline__ void pdl_wait_and_release() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
