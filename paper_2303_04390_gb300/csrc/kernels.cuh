@@ -949,6 +949,36 @@ pre_u20_kernel(LevelArgs<float> a) {
     for (int s = 0; s < SP; ++s) den = fmaf(q[u][s] * ux[1][s], ux[0][s], den);
     float num[2];
     typename A::type g[2];
+    // Both children stored: a_0' Q and a_1' Q in one pass over Q's rows (the
+    // same operations in the same order as one rowcomb2 per child).
+    const bool both_q = in[u][0].y < 0 && in[u][1].y < 0;
+    if (both_q) {
+      float2 w0[SP / 2], w1[SP / 2];
+#pragma unroll
+      for (int p = 0; p < SP / 2; ++p) w0[p] = w1[p] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < SP; ++i) {
+        const float2 a0 = make_float2(q[u][i] * ux[1][i], q[u][i] * ux[1][i]);
+        const float2 a1 = make_float2(q[u][i] * ux[0][i], q[u][i] * ux[0][i]);
+        const float2* row = reinterpret_cast<const float2*>(Qm + i * SP);
+#pragma unroll
+        for (int p = 0; p < SP / 2; ++p) {
+          const float2 qr = row[p];
+          w0[p] = __ffma2_rn(qr, a0, w0[p]);
+          w1[p] = __ffma2_rn(qr, a1, w1[p]);
+        }
+      }
+      float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+      for (int p = 0; p < SP / 2; ++p) {
+        n0 = fmaf(w0[p].x, ux[0][2 * p], n0);
+        n0 = fmaf(w0[p].y, ux[0][2 * p + 1], n0);
+        n1 = fmaf(w1[p].x, ux[1][2 * p], n1);
+        n1 = fmaf(w1[p].y, ux[1][2 * p + 1], n1);
+      }
+      num[0] = n0 * gam;
+      num[1] = n1 * gam;
+    }
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
       float av[SP];  // a_x = q_k o U_y
@@ -956,7 +986,9 @@ pre_u20_kernel(LevelArgs<float> a) {
       for (int s = 0; s < SP; ++s) av[s] = q[u][s] * ux[1 - x][s];
       const int y = in[u][x].y;
       float nx = 0.f;
-      if (y >= 0) {  // compact tip: a_x' dP_x e_y, from row y of dP' (0 for a gap)
+      if (both_q) {
+        nx = num[x];
+      } else if (y >= 0) {  // compact tip: a_x' dP_x e_y, from row y of dP' (0 for a gap)
         if (y < S) {
           const float* Dt = mats + ((NS * u + 2 + x) * RP + rr) * MS;
 #pragma unroll
